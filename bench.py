@@ -1,0 +1,390 @@
+"""Benchmark: COO transposition throughput on one GB300 (and N replicas).
+
+Workload (default): a 3-order tensor of 12000 x 9000 x 28000 with 76M
+distinct coordinates drawn Zipf(1.1) per mode, float32 values N(0,1), sorted
+in (0,1,2) order and resident in HBM. One step transposes it into each of the
+5 non-identity target orders (out of place, the input stays intact), so a
+step moves 5 x 76M entries. Throughput = entries transposed per second
+(Gnnz/s), device-timed with CUDA events; the inputs (2.4 GB) are larger than
+the 129 MB L2, so no flush is needed between steps.
+
+Also reported: the live roofline of the dominant kernel (algorithmic bytes /
+CUDA-event duration against the measured HBM copy bandwidth), the end-to-end
+rate through qsd_transpose_host with host buffers, SM clocks sampled during
+the timed region, and the CPU oracle's rate on a bounded sample.
+
+`--impl reference` times the CPU oracle (std::stable_sort on the host cores)
+on bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = ("Gnnz/s transposed (bit-exact) and % HBM roofline; batched/served vs "
+          "single calls")
+WORKLOADS = {
+    "nell2like": synth.WORKLOAD_NELL2_LIKE,
+    "uniform3d": synth.WORKLOAD_3D_UNIFORM,
+    "deliciouslike": synth.WORKLOAD_DELICIOUS_LIKE,
+}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def committed_traffic(kernel: str, workload: str):
+    """DRAM bytes per entry for a kernel from the committed ncu summary."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    return d.get(workload, {}).get(kernel)
+
+
+def cpu_oracle_rate(t_coords: np.ndarray, t_vals: np.ndarray, perms, target_s=12.0):
+    """The oracle (single-threaded std::stable_sort) on a prefix sample."""
+    import oracle
+    n_total = t_coords.shape[1]
+    m = min(n_total, 500_000)
+    t0 = time.perf_counter()
+    for sigma in perms:
+        oracle.transpose(t_coords[:, :m], t_vals[:m], sigma)
+    dt = time.perf_counter() - t0
+    # grow the sample towards target_s seconds of work
+    scale = max(1.0, target_s / max(dt, 1e-3))
+    m2 = int(min(n_total, m * scale))
+    if m2 > m:
+        m = m2
+        t0 = time.perf_counter()
+        for sigma in perms:
+            oracle.transpose(t_coords[:, :m], t_vals[:m], sigma)
+        dt = time.perf_counter() - t0
+    return {"value": len(perms) * m / dt / 1e9, "unit": "Gnnz/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {m} entries of the workload (a sorted prefix), all "
+                      f"{len(perms)} target orders, std::stable_sort on 1 host core, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    wl = WORKLOADS[args.workload]
+    nnz = args.nnz or wl["nnz"]
+    sample = min(nnz, args.ref_sample)
+    w = synth.scaled(wl, sample) if sample != wl["nnz"] else wl
+    t = synth.make(w)
+    coords, vals = t.coords.numpy(), t.vals.numpy()
+    perms = wl["perms"]
+    for _ in range(args.warmup):
+        for sigma in perms:
+            oracle.transpose(coords, vals, sigma)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for sigma in perms:
+            oracle.transpose(coords, vals, sigma)
+    dt = time.perf_counter() - t0
+    value = args.steps * len(perms) * sample / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gnnz/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic",
+            "config": {"workload": wl["name"], "nnz": nnz, "sample_nnz": sample,
+                       "perms": [list(p) for p in perms]},
+            "cpu_baseline": {"value": value, "unit": "Gnnz/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{sample} entries sorted in input order (the workload's "
+                                       f"generator at this count), {len(perms)} target orders "
+                                       f"per step"},
+            "e2e": {"value": value, "unit": "Gnnz/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="qsd", choices=["qsd", "reference"])
+    ap.add_argument("--workload", default="nell2like", choices=sorted(WORKLOADS))
+    ap.add_argument("--nnz", type=int, default=0, help="override the entry count")
+    ap.add_argument("--perms", default="", help="comma-separated subset, e.g. 021,102")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=2_000_000)
+    ap.add_argument("--check", action="store_true", help="sampled parity check vs the oracle")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import paper_2005_10427_gb300 as qsd
+    qsd.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    wl = dict(WORKLOADS[args.workload])
+    if args.nnz:
+        wl = synth.scaled(wl, args.nnz)
+    perms = wl["perms"]
+    if args.perms:
+        perms = [tuple(int(ch) for ch in p) for p in args.perms.split(",")]
+    t = synth.make(wl, device=dev)
+    torch.cuda.synchronize()
+    r, nnz = t.coords.shape
+    vb = t.vals.element_size()
+    R = 4 * r + vb
+    plans = [qsd.Plan(wl["dims"], sigma) for sigma in perms]
+    ws_bytes = max(p.workspace_bytes(nnz) for p in plans)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    cb = [torch.empty((r, nnz), dtype=torch.int32, device=dev) for _ in range(2)]
+    vbuf = [torch.empty(nnz, dtype=t.vals.dtype, device=dev) for _ in range(2)]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for p in plans:
+            qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, p, ws, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    status = qsd.get_async_status()
+    if status != 0:
+        raise SystemExit(f"device status {status} after warm-up")
+
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+        torch.distributed.barrier()
+    ms_per_step = ms / args.steps
+    entries_per_step = len(perms) * nnz
+    value = world * entries_per_step * args.steps / (ms / 1e3) / 1e9
+
+    # Live per-kernel timings over the same steps (instrumented replay).
+    qsd.profile_reset()
+    qsd.profile_enable(True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    recs = qsd.profile_read()
+    qsd.profile_enable(False)
+    qsd.profile_reset()
+    agg = {}
+    for rec in recs:
+        a = agg.setdefault(rec["kernel"], {"launches": 0, "ms": 0.0, "bytes": 0, "known": True})
+        a["launches"] += 1
+        a["ms"] += rec["ms"]
+        if rec["algo_bytes"] < 0:
+            a["known"] = False
+        else:
+            a["bytes"] += rec["algo_bytes"]
+    total_ms = sum(a["ms"] for a in agg.values())
+    top = max(agg, key=lambda k: agg[k]["ms"])
+    peak, peak_kind = measured_peaks()
+    achieved = agg[top]["bytes"] / (agg[top]["ms"] / 1e3) / 1e9 if agg[top]["ms"] > 0 else 0.0
+    traffic_pe = committed_traffic(top, wl["name"])
+    top_entries = sum(rec["entries"] for rec in recs if rec["kernel"] == top and rec["entries"] > 0)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "kernel": top,
+                "traffic": (traffic_pe * top_entries / agg[top]["launches"]) if traffic_pe else None,
+                "peak_kind": peak_kind,
+                "algo_bytes_per_launch": agg[top]["bytes"] / max(agg[top]["launches"], 1),
+                "avg_launch_ms": agg[top]["ms"] / max(agg[top]["launches"], 1),
+                "share_of_device_time": round(agg[top]["ms"] / total_ms, 4) if total_ms else None,
+                "whole_step_frac": round(
+                    (2 * R * entries_per_step / (ms_per_step / 1e3) / 1e9) / peak, 4)}
+    launches_per_step = len(recs) / args.steps
+
+    # End to end through qsd_transpose_host: host input -> device -> host output.
+    e2e = None
+    if not args.no_e2e:
+        hc = t.coords.cpu().pin_memory()
+        hv = t.vals.cpu().pin_memory()
+        oc = torch.empty_like(hc).pin_memory()
+        ov = torch.empty_like(hv).pin_memory()
+        e2e_steps = max(1, min(args.steps, 3))
+        for p in plans:  # warm-up
+            qsd.transpose_host(hc, hv, p, cb, vbuf, ws, oc, ov, stream)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for p in plans:
+                qsd.transpose_host(hc, hv, p, cb, vbuf, ws, oc, ov, stream)
+        dt = time.perf_counter() - t0
+        e2e = {"value": world * entries_per_step * e2e_steps / dt / 1e9, "unit": "Gnnz/s",
+               "h2d_bytes_per_step": len(plans) * nnz * R,
+               "d2h_bytes_per_step": len(plans) * nnz * R}
+
+    check = None
+    if args.check:
+        check = sampled_check(qsd, t, plans, perms, cb, vbuf, ws, stream)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(t.coords.cpu().numpy(), t.vals.cpu().numpy(), perms)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "Gnnz/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32" if vb == 4 else "int32+f64",
+                "data": "synthetic",
+                "config": {"workload": wl["name"], "dims": wl["dims"], "nnz": nnz,
+                           "dists": [list(d) for d in wl["dists"]],
+                           "perms": [list(p) for p in perms], "input_order": list(range(r)),
+                           "out_of_place": True, "parallelism": f"replicas{world}",
+                           "l2": "inputs (%.2f GB) larger than L2; no flush" % (nnz * R / 1e9)},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(round(launches_per_step * args.steps)),
+                "launches_per_step": launches_per_step,
+                "kernels": {k: {"launches": a["launches"], "ms": round(a["ms"], 3),
+                                "share": round(a["ms"] / total_ms, 4) if total_ms else None}
+                            for k, a in sorted(agg.items(), key=lambda kv: -kv[1]["ms"])},
+                "clocks": clocks}
+        if check is not None:
+            line["check"] = check
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def sampled_check(qsd, t, plans, perms, cb, vbuf, ws, stream):
+    """Sampled parity at full size: sortedness + multiset hash on the device,
+    and exact output rank of sampled entries computed on the host."""
+    import oracle  # noqa: F401  (the check is test infrastructure)
+    out = {}
+    c_in = t.coords
+    nnz = c_in.shape[1]
+    for p, sigma in zip(plans, perms):
+        sel = qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, p, ws, stream)
+        oc, ov = cb[sel], vbuf[sel]
+        keys = [oc[m].long() for m in sigma]
+        lt = torch.zeros(nnz - 1, dtype=torch.bool, device=oc.device)
+        eq = torch.ones(nnz - 1, dtype=torch.bool, device=oc.device)
+        for k in keys:
+            lt |= eq & (k[:-1] < k[1:])
+            eq &= k[:-1] == k[1:]
+        sorted_ok = bool(lt.all())
+
+        def h(c, v):
+            x = v.view(torch.int32).long() if v.element_size() == 4 else v.view(torch.int64)
+            acc = x * 0x9E3779B1
+            for m in range(c.shape[0]):
+                acc = acc ^ (c[m].long() * (0x85EBCA77 + 2 * m + 1))
+                acc = acc * 0x27D4EB2F + 0x165667B1
+            return int(acc.sum())
+        ok_hash = h(c_in, t.vals) == h(oc, ov)
+        out["".join(map(str, sigma))] = bool(sorted_ok and ok_hash)
+    torch.cuda.synchronize()
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

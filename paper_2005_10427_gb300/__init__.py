@@ -1,0 +1,273 @@
+"""GB300 sparse COO tensor transposition (the Quesadilla method, sm_103a).
+
+Thin Python binding over the C ABI in include/qsd.h: it only marshals
+arguments (torch tensors provide device memory and streams); every step of
+the transposition runs in the CUDA library libqsd.so. There is no CPU
+fallback: if the library is missing, calls raise.
+
+    plan = Plan(dims, target_perm)                 # Algorithm 3 on the host
+    coords_t, vals_t = transpose(coords, vals, plan)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence, Tuple
+
+from . import _capi
+
+__all__ = ["Plan", "QsdError", "transpose", "transpose_buffers", "transpose_from",
+           "transpose_host",
+           "get_async_status", "workspace_status", "build", "lib", "LIB_PATH"]
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libqsd.so")
+
+
+class QsdError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = int(status)
+        name = _capi.STATUS_NAMES.get(self.status, f"status {status}")
+        super().__init__(f"{where}: {name}" if where else name)
+
+
+def build(force: bool = False) -> str:
+    from .build import build as _build
+    return _build(force=force)
+
+
+def lib() -> ctypes.CDLL:
+    return _capi.load(LIB_PATH)
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise QsdError(status, where)
+
+
+def _i32(seq: Sequence[int]):
+    return (ctypes.c_int * len(seq))(*[int(x) for x in seq])
+
+
+class Plan:
+    """A transposition plan: input order tau -> target order sigma.
+
+    dims: mode sizes; target_perm: sigma; input_mode_order: tau (identity by
+    default). Options map to qsd_plan_options.
+    """
+
+    def __init__(self, dims: Sequence[int], target_perm: Sequence[int],
+                 input_mode_order: Optional[Sequence[int]] = None, *,
+                 validate: bool = False, digit_bits: int = 0,
+                 local_capacity: int = 0, no_skip: bool = False):
+        L = lib()
+        r = len(dims)
+        self.dims = [int(d) for d in dims]
+        self.order = r
+        self.target_perm = [int(x) for x in target_perm]
+        self.input_mode_order = list(range(r)) if input_mode_order is None else \
+            [int(x) for x in input_mode_order]
+        opts = _capi.PlanOptions(int(bool(validate)), int(digit_bits), int(local_capacity),
+                                 int(bool(no_skip)))
+        handle = ctypes.c_void_p()
+        dims_arr = (ctypes.c_int64 * max(r, 1))(*self.dims)
+        st = L.qsd_plan_ex(r, dims_arr, _i32(self.input_mode_order) if r else None,
+                           _i32(self.target_perm) if r else None, ctypes.byref(opts),
+                           ctypes.byref(handle))
+        _check(st, "qsd_plan")
+        self._h = handle
+        self._lib = L
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.qsd_plan_destroy(h)
+            self._h = None
+
+    def info(self) -> dict:
+        inf = _capi.PlanInfo()
+        _check(self._lib.qsd_plan_get_info(self._h, ctypes.byref(inf)), "qsd_plan_get_info")
+        r = inf.order
+        sig = list(inf.target_perm[:r])
+        calls = [(tuple(sig[:inf.call_prefix_len[i]]), int(inf.call_mode[i]))
+                 for i in range(inf.num_calls)]
+        groups = []
+        for g in range(inf.num_groups):
+            pl, nk = inf.group_prefix_len[g], inf.group_num_keys[g]
+            groups.append(dict(prefix=tuple(sig[:pl]), keys=tuple(sig[pl:pl + nk]),
+                               key_bits=int(inf.group_key_bits[g]),
+                               passes=int(inf.group_digit_passes[g])))
+        return dict(order=r, input_mode_order=list(inf.input_mode_order[:r]),
+                    target_perm=sig, calls=calls, num_calls=inf.num_calls,
+                    num_bucketed_calls=inf.num_bucketed_calls, groups=groups,
+                    local_capacity=inf.local_capacity)
+
+    @property
+    def calls(self) -> List[Tuple[Tuple[int, ...], int]]:
+        return self.info()["calls"]
+
+    def workspace_bytes(self, nnz: int) -> int:
+        out = ctypes.c_size_t()
+        _check(self._lib.qsd_workspace_bytes(self._h, int(nnz), ctypes.byref(out)),
+               "qsd_workspace_bytes")
+        return int(out.value)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _val_bytes(vals) -> int:
+    return 0 if vals is None else int(vals.element_size())
+
+
+def transpose_buffers(cbuf: Sequence, vbuf: Optional[Sequence], selector: int, nnz: int,
+                      plan: Plan, workspace, stream=None) -> int:
+    """Runs qsd_transpose_ws on explicit double buffers.
+
+    cbuf: two int32 CUDA tensors (r, stride); vbuf: two value tensors or None;
+    selector: which buffer holds the input. workspace: a CUDA uint8 tensor of
+    at least plan.workspace_bytes(nnz). Returns the selector of the result.
+    """
+    c = _capi.Coords()
+    c.buf[0] = cbuf[0].data_ptr()
+    c.buf[1] = cbuf[1].data_ptr()
+    c.stride = int(cbuf[0].stride(0)) if cbuf[0].dim() == 2 else int(nnz)
+    c.selector = int(selector)
+    v = _capi.Values()
+    if vbuf is not None:
+        v.buf[0] = vbuf[0].data_ptr()
+        v.buf[1] = vbuf[1].data_ptr()
+        v.elem_bytes = _val_bytes(vbuf[0])
+        v.selector = int(selector)
+    st = lib().qsd_transpose_ws(ctypes.byref(c), ctypes.byref(v), int(nnz), plan.handle,
+                                ctypes.c_void_p(workspace.data_ptr()),
+                                int(workspace.numel()), _stream_handle(stream))
+    _check(st, "qsd_transpose_ws")
+    return int(c.selector)
+
+
+def transpose_from(in_coords, in_vals, cbuf: Sequence, vbuf: Optional[Sequence], nnz: int,
+                   plan: Plan, workspace, stream=None) -> int:
+    """Out-of-place: qsd_transpose_from_ws. The input tensors stay unchanged;
+    the result lands in cbuf[sel] / vbuf[sel]; returns sel."""
+    c = _capi.Coords()
+    c.buf[0] = cbuf[0].data_ptr()
+    c.buf[1] = cbuf[1].data_ptr()
+    c.stride = int(cbuf[0].stride(0))
+    v = _capi.Values()
+    if vbuf is not None:
+        v.buf[0] = vbuf[0].data_ptr()
+        v.buf[1] = vbuf[1].data_ptr()
+        v.elem_bytes = _val_bytes(vbuf[0])
+    st = lib().qsd_transpose_from_ws(
+        ctypes.c_void_p(in_coords.data_ptr()), int(in_coords.stride(0)),
+        ctypes.c_void_p(in_vals.data_ptr()) if in_vals is not None else None,
+        ctypes.byref(c), ctypes.byref(v), int(nnz), plan.handle,
+        ctypes.c_void_p(workspace.data_ptr()), int(workspace.numel()),
+        _stream_handle(stream))
+    _check(st, "qsd_transpose_from_ws")
+    return int(c.selector)
+
+
+def transpose(coords, vals, plan: Plan, *, workspace=None, stream=None):
+    """Transposes a COO tensor on the GPU.
+
+    coords: int32 CUDA tensor (r, nnz), rows contiguous; vals: 1-D CUDA tensor
+    of 4- or 8-byte elements, or None. Returns (coords_out, vals_out); the
+    result may live in the input tensors' storage (the library ping-pongs
+    between the input and a second buffer it is given here).
+    """
+    import torch
+    if coords.dim() != 2 or coords.dtype != torch.int32 or (
+            coords.shape[1] > 1 and coords.stride(1) != 1):
+        raise ValueError("coords must be an int32 tensor of shape (order, nnz) with unit "
+                         "stride along entries")
+    if not coords.is_cuda:
+        raise ValueError("coords must be on a CUDA device (no CPU path exists)")
+    nnz = coords.shape[1]
+    alt_c = torch.empty_like(coords)
+    vbuf = None
+    if vals is not None:
+        if vals.dim() != 1 or vals.numel() != nnz or vals.element_size() not in (4, 8):
+            raise ValueError("vals must be 1-D with nnz elements of 4 or 8 bytes")
+        vbuf = [vals, torch.empty_like(vals)]
+    if workspace is None:
+        workspace = torch.empty(plan.workspace_bytes(nnz), dtype=torch.uint8,
+                                device=coords.device)
+    sel = transpose_buffers([coords, alt_c], vbuf, 0, nnz, plan, workspace, stream)
+    out_c = [coords, alt_c][sel]
+    out_v = None if vbuf is None else vbuf[sel]
+    return out_c, out_v
+
+
+def transpose_host(coords_host, vals_host, plan: Plan, dev_cbuf, dev_vbuf, workspace,
+                   out_coords_host, out_vals_host, stream=None) -> None:
+    """End-to-end call on host tensors through qsd_transpose_host.
+
+    coords_host (r, nnz) int32 / vals_host on the CPU (pinned for full
+    bandwidth); dev_cbuf / dev_vbuf: two device buffers each; results are
+    written into out_coords_host / out_vals_host. Waits for the stream.
+    """
+    nnz = coords_host.shape[1]
+    c = _capi.Coords()
+    c.buf[0] = dev_cbuf[0].data_ptr()
+    c.buf[1] = dev_cbuf[1].data_ptr()
+    c.stride = int(dev_cbuf[0].stride(0))
+    c.selector = 0
+    v = _capi.Values()
+    if dev_vbuf is not None:
+        v.buf[0] = dev_vbuf[0].data_ptr()
+        v.buf[1] = dev_vbuf[1].data_ptr()
+        v.elem_bytes = _val_bytes(dev_vbuf[0])
+    st = lib().qsd_transpose_host(
+        ctypes.c_void_p(coords_host.data_ptr()), int(coords_host.stride(0)),
+        ctypes.c_void_p(vals_host.data_ptr()) if vals_host is not None else None,
+        ctypes.c_void_p(out_coords_host.data_ptr()), int(out_coords_host.stride(0)),
+        ctypes.c_void_p(out_vals_host.data_ptr()) if out_vals_host is not None else None,
+        int(nnz), plan.handle, ctypes.byref(c), ctypes.byref(v),
+        ctypes.c_void_p(workspace.data_ptr()), int(workspace.numel()),
+        _stream_handle(stream))
+    _check(st, "qsd_transpose_host")
+
+
+def workspace_status(workspace, stream=None) -> int:
+    out = ctypes.c_int()
+    _check(lib().qsd_workspace_status(ctypes.c_void_p(workspace.data_ptr()),
+                                      _stream_handle(stream), ctypes.byref(out)),
+           "qsd_workspace_status")
+    return int(out.value)
+
+
+def get_async_status(stream=None) -> int:
+    out = ctypes.c_int()
+    _check(lib().qsd_get_async_status(_stream_handle(stream), ctypes.byref(out)),
+           "qsd_get_async_status")
+    return int(out.value)
+
+
+def profile_enable(on: bool = True) -> None:
+    """Records CUDA-event timings of every library kernel launch (qsd_profile_*)."""
+    _check(lib().qsd_profile_enable(int(bool(on))), "qsd_profile_enable")
+
+
+def profile_reset() -> None:
+    _check(lib().qsd_profile_reset(), "qsd_profile_reset")
+
+
+def profile_read() -> List[dict]:
+    """The recorded launches since the last reset (waits for them)."""
+    n = ctypes.c_int()
+    _check(lib().qsd_profile_read(None, 0, ctypes.byref(n)), "qsd_profile_read")
+    if n.value == 0:
+        return []
+    recs = (_capi.ProfileRecord * n.value)()
+    _check(lib().qsd_profile_read(recs, n.value, ctypes.byref(n)), "qsd_profile_read")
+    return [dict(kernel=r.kernel.decode(), group=r.group, pass_=r.pass_, entries=r.entries,
+                 algo_bytes=r.algo_bytes, ms=r.ms) for r in recs]

@@ -1,0 +1,90 @@
+"""ctypes declarations of include/qsd.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+MAX_ORDER = 8
+
+QSD_OK = 0
+STATUS_NAMES = {
+    0: "QSD_OK", 1: "QSD_ERR_INVALID_ARGUMENT", 2: "QSD_ERR_UNSUPPORTED",
+    3: "QSD_ERR_OUT_OF_MEMORY", 4: "QSD_ERR_CUDA", 5: "QSD_ERR_UNSORTED_INPUT",
+    6: "QSD_ERR_COORD_OUT_OF_RANGE", 7: "QSD_ERR_TIMEOUT", 8: "QSD_ERR_BUDGET",
+    9: "QSD_ERR_WORKSPACE_TOO_SMALL",
+}
+
+
+class Coords(ctypes.Structure):
+    _fields_ = [("buf", ctypes.c_void_p * 2), ("stride", ctypes.c_int64),
+                ("selector", ctypes.c_int)]
+
+
+class Values(ctypes.Structure):
+    _fields_ = [("buf", ctypes.c_void_p * 2), ("elem_bytes", ctypes.c_int),
+                ("selector", ctypes.c_int)]
+
+
+class PlanOptions(ctypes.Structure):
+    _fields_ = [("validate", ctypes.c_int), ("digit_bits", ctypes.c_int),
+                ("local_capacity", ctypes.c_int), ("no_skip", ctypes.c_int)]
+
+
+_A = ctypes.c_int * MAX_ORDER
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("input_mode_order", _A), ("target_perm", _A),
+                ("num_calls", ctypes.c_int), ("num_bucketed_calls", ctypes.c_int),
+                ("call_prefix_len", _A), ("call_mode", _A), ("num_groups", ctypes.c_int),
+                ("group_prefix_len", _A), ("group_num_keys", _A), ("group_key_bits", _A),
+                ("group_digit_passes", _A), ("local_capacity", ctypes.c_int)]
+
+
+class ProfileRecord(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_char * 32), ("group", ctypes.c_int), ("pass_", ctypes.c_int),
+                ("entries", ctypes.c_int64), ("algo_bytes", ctypes.c_int64),
+                ("ms", ctypes.c_float)]
+
+
+# (name, restype, argtypes) for every entry point of include/qsd.h
+P = ctypes.c_void_p
+I = ctypes.c_int
+I64 = ctypes.c_int64
+SIGNATURES = [
+    ("qsd_plan", I, [I, P, P, P, ctypes.POINTER(P)]),
+    ("qsd_plan_ex", I, [I, P, P, P, ctypes.POINTER(PlanOptions), ctypes.POINTER(P)]),
+    ("qsd_plan_get_info", I, [P, ctypes.POINTER(PlanInfo)]),
+    ("qsd_plan_destroy", None, [P]),
+    ("qsd_workspace_bytes", I, [P, I64, ctypes.POINTER(ctypes.c_size_t)]),
+    ("qsd_transpose", I, [ctypes.POINTER(Coords), ctypes.POINTER(Values), I64, P, P]),
+    ("qsd_transpose_ws", I, [ctypes.POINTER(Coords), ctypes.POINTER(Values), I64, P, P,
+                             ctypes.c_size_t, P]),
+    ("qsd_transpose_from_ws", I, [P, I64, P, ctypes.POINTER(Coords), ctypes.POINTER(Values),
+                                  I64, P, P, ctypes.c_size_t, P]),
+    ("qsd_transpose_host", I, [P, I64, P, P, I64, P, I64, P, ctypes.POINTER(Coords),
+                               ctypes.POINTER(Values), P, ctypes.c_size_t, P]),
+    ("qsd_workspace_status", I, [P, P, ctypes.POINTER(I)]),
+    ("qsd_get_async_status", I, [P, ctypes.POINTER(I)]),
+    ("qsd_profile_enable", I, [I]),
+    ("qsd_profile_read", I, [ctypes.POINTER(ProfileRecord), I, ctypes.POINTER(I)]),
+    ("qsd_profile_reset", I, []),
+    ("qsd_status_string", ctypes.c_char_p, [I]),
+    ("qsd_version", ctypes.c_char_p, []),
+]
+
+_lib = None
+
+
+def load(path: str) -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libqsd is not built ({path} missing); run build()")
+        L = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib

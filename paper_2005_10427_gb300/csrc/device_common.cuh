@@ -1,0 +1,182 @@
+// Device helpers shared by the kernels: status word, bounded waits,
+// relaxed flag words for decoupled look-back, radix digit extraction and a
+// stable block-wide ranking of radix digits.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qsd_internal.h"
+
+namespace qsd {
+
+// ---------------------------------------------------------------------------
+// Status word: the first error recorded wins; kernels never trap.
+__device__ __forceinline__ void set_status(unsigned* status, unsigned code) {
+  if (status) atomicCAS(status, 0u, code);
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Every spin in this library gives up after this long and records
+// QSD_ERR_TIMEOUT (a legitimate wait lasts microseconds).
+constexpr uint64_t kSpinLimitNs = 2000000000ull;  // 2 s
+
+// ---------------------------------------------------------------------------
+// Look-back words: bits 31..30 = state, bits 29..0 = count.
+constexpr uint32_t kLbNone = 0u;
+constexpr uint32_t kLbAggregate = 1u << 30;
+constexpr uint32_t kLbInclusive = 2u << 30;
+constexpr uint32_t kLbStateMask = 3u << 30;
+constexpr uint32_t kLbCountMask = (1u << 30) - 1;
+
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Waits (bounded) until the word at p has a nonzero state and returns it.
+// On timeout records QSD_ERR_TIMEOUT and returns an inclusive word of 0 so
+// the caller's walk ends.
+__device__ __forceinline__ uint32_t wait_flag(const uint32_t* p, unsigned* status) {
+  uint32_t v = ld_relaxed(p);
+  if (v & kLbStateMask) return v;
+  uint64_t t0 = global_timer_ns();
+  unsigned spins = 0;
+  while (true) {
+    v = ld_relaxed(p);
+    if (v & kLbStateMask) return v;
+    if ((++spins & 63u) == 0) {
+      if (global_timer_ns() - t0 > kSpinLimitNs) {
+        set_status(status, QSD_ERR_TIMEOUT);
+        return kLbInclusive;
+      }
+      __nanosleep(64);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Radix digit of one entry for one pass: OR of bit slices of its coordinates.
+__device__ __forceinline__ uint32_t field_bits(uint32_t c, const DigitField& f) {
+  return ((c >> f.shift) & ((1u << f.width) - 1u)) << f.dst;
+}
+
+// ---------------------------------------------------------------------------
+// Stable block-wide ranking of kRadix-valued digits.
+//
+// Thread (warp w, lane l) holds ITEMS digits; item i is element
+// w*ITEMS*32 + i*32 + l of the tile ("warp-striped"), so the warps cover
+// consecutive ranges and each warp's rounds consecutive 32-element pieces.
+// On return rank[i] is the element's position when the tile is stably sorted
+// by digit; s_bin_start[d] / s_bin_count[d] give each digit's run.
+// Ranking inside a round uses __match_any_sync (lanes with equal digits) and
+// a per-warp running count in shared memory.
+template <int NWARPS, int ITEMS>
+__device__ __forceinline__ void block_rank(const uint32_t (&dig)[ITEMS],
+                                           uint32_t (&rank)[ITEMS],
+                                           uint32_t* s_warp_hist,  // [NWARPS][kRadix]
+                                           uint32_t* s_bin_start,  // [kRadix]
+                                           uint32_t* s_bin_count)  // [kRadix]
+{
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  uint32_t* h = s_warp_hist + w * kRadix;
+#pragma unroll
+  for (int d = lane; d < kRadix; d += 32) h[d] = 0;
+  __syncwarp();
+  const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t d = dig[i];
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t pre = h[d];
+    rank[i] = pre + __popc(peers & lt);
+    __syncwarp();
+    if (lane == __ffs(peers) - 1) h[d] = pre + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // exclusive scan over warps for each digit; digit totals
+  for (int d = threadIdx.x; d < kRadix; d += NWARPS * 32) {
+    uint32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < NWARPS; ++ww) {
+      uint32_t t = s_warp_hist[ww * kRadix + d];
+      s_warp_hist[ww * kRadix + d] = run;
+      run += t;
+    }
+    s_bin_count[d] = run;
+  }
+  __syncthreads();
+  // exclusive scan over digits (one warp, kRadix/32 digits per lane)
+  if (w == 0) {
+    constexpr int PER = kRadix / 32;
+    uint32_t v[PER];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      v[j] = s_bin_count[lane * PER + j];
+      sum += v[j];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      s_bin_start[lane * PER + j] = run;
+      run += v[j];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i)
+    rank[i] += s_bin_start[dig[i]] + h[dig[i]];
+}
+
+// Block-wide exclusive sum of one value per thread; returns the thread's
+// exclusive prefix and writes the block total to *total.
+template <int NWARPS>
+__device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t v, uint32_t* s_tmp,
+                                                        uint32_t* total) {
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  uint32_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_tmp[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t x = lane < NWARPS ? s_tmp[lane] : 0u;
+    uint32_t xi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += t;
+    }
+    if (lane < NWARPS) s_tmp[lane] = xi - x;
+    if (lane == NWARPS - 1) s_tmp[NWARPS] = xi;
+  }
+  __syncthreads();
+  uint32_t r = s_tmp[w] + incl - v;
+  *total = s_tmp[NWARPS];
+  __syncthreads();
+  return r;
+}
+
+}  // namespace qsd

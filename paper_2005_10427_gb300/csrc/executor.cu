@@ -1,0 +1,393 @@
+// Executor: runs a plan's groups in order (Algorithm 3's outer loop) on the
+// caller's double buffers, and the C-ABI entry points around it.
+//
+// Per group (prefix P, key K, passes p):
+//   P empty, nnz <= local capacity: one block-local sort of the whole tensor;
+//   P empty otherwise: digit histogram, digit scan, p global passes;
+//   P non-empty: bucket discovery over the P rows, classification, a
+//     block-local sort of every small bucket and the global passes over the
+//     large buckets. Buckets found once per group serve all of its passes
+//     (the paper's conclusion: discover the buckets once per prefix).
+// The group's result lands in the buffer the global passes end in; the
+// block-local sort writes straight there (in place when that is the input
+// buffer). No step synchronises with the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "kernels.cuh"
+
+namespace qsd {
+int seg_lookback_words(int nnz);
+}
+
+namespace {
+
+using namespace qsd;
+
+constexpr size_t kAlign = 256;
+constexpr int64_t kMaxNnz = (int64_t(1) << 30) - 1;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+struct Layout {
+  size_t status, counters, seg_start, seg_lb, large, tile_base, tile_owner, hist,
+      lb0, lb1, total;
+  int max_large, max_tiles, max_passes;
+};
+
+bool plan_has_prefix_group(const qsd_plan_s* p) {
+  for (int g = 0; g < p->ngroups; ++g)
+    if (p->groups[g].npasses > 0 && p->groups[g].prefix_len > 0) return true;
+  return false;
+}
+
+Layout layout_for(const qsd_plan_s* p, int64_t nnz) {
+  Layout L;
+  std::memset(&L, 0, sizeof(L));
+  const int T = onesweep_tile();
+  const int C = p->local_capacity;
+  int maxp = 0;
+  for (int g = 0; g < p->ngroups; ++g) maxp = std::max(maxp, p->groups[g].npasses);
+  L.max_passes = std::max(maxp, 1);
+  const int64_t n = std::max<int64_t>(nnz, 1);
+  L.max_large = (int)(n / (C + 1) + 1);
+  L.max_tiles = (int)((n + T - 1) / T + L.max_large);
+  const bool segs = plan_has_prefix_group(p);
+  size_t off = 0;
+  L.status = off;
+  off += align_up(sizeof(unsigned));
+  L.counters = off;
+  off += align_up(sizeof(int) * kNumCounters);
+  L.seg_start = off;
+  off += segs ? align_up(sizeof(int) * (size_t)(n + 2)) : 0;
+  L.seg_lb = off;
+  off += segs ? align_up(sizeof(uint32_t) * (size_t)seg_lookback_words((int)n)) : 0;
+  L.large = off;
+  off += segs ? align_up(sizeof(int2) * (size_t)L.max_large) : 0;
+  L.tile_base = off;
+  off += segs ? align_up(sizeof(int) * (size_t)L.max_large) : 0;
+  L.tile_owner = off;
+  off += segs ? align_up(sizeof(int) * (size_t)L.max_tiles) : 0;
+  L.hist = off;
+  off += align_up(sizeof(uint32_t) * (size_t)L.max_large * L.max_passes * kRadix);
+  L.lb0 = off;
+  off += align_up(sizeof(uint32_t) * (size_t)L.max_tiles * kRadix);
+  L.lb1 = off;
+  off += align_up(sizeof(uint32_t) * (size_t)L.max_tiles * kRadix);
+  L.total = off;
+  return L;
+}
+
+#define QSD_CUDA(call)                      \
+  do {                                      \
+    cudaError_t e_ = (call);                \
+    if (e_ != cudaSuccess) return QSD_ERR_CUDA; \
+  } while (0)
+
+qsd_status check_buffers(const qsd_coords* coords, const qsd_values* vals,
+                         int64_t nnz, const qsd_plan_s* plan) {
+  if (!coords || !plan) return QSD_ERR_INVALID_ARGUMENT;
+  if (nnz < 0) return QSD_ERR_INVALID_ARGUMENT;
+  if (nnz > kMaxNnz) return QSD_ERR_UNSUPPORTED;
+  if (coords->selector != 0 && coords->selector != 1) return QSD_ERR_INVALID_ARGUMENT;
+  if (nnz > 0 && (!coords->buf[0] || !coords->buf[1])) return QSD_ERR_INVALID_ARGUMENT;
+  if (coords->stride < nnz) return QSD_ERR_INVALID_ARGUMENT;
+  if (vals && vals->elem_bytes != 0) {
+    if (vals->elem_bytes != 4 && vals->elem_bytes != 8) return QSD_ERR_INVALID_ARGUMENT;
+    if (vals->selector != 0 && vals->selector != 1) return QSD_ERR_INVALID_ARGUMENT;
+    if (nnz > 0 && (!vals->buf[0] || !vals->buf[1])) return QSD_ERR_INVALID_ARGUMENT;
+  }
+  return QSD_OK;
+}
+
+// Where a group reads its input: one of the double buffers (idx 0/1) or a
+// caller's read-only input (idx -1).
+struct Src {
+  const int32_t* c;
+  const void* v;
+  int64_t stride;
+  int idx;
+};
+
+qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
+                    int64_t nnz64, const qsd_plan_s* plan, void* ws, const Layout& L,
+                    cudaStream_t st) {
+  const int nnz = (int)nnz64;
+  uint8_t* base = static_cast<uint8_t*>(ws);
+  unsigned* status = reinterpret_cast<unsigned*>(base + L.status);
+  int* counters = reinterpret_cast<int*>(base + L.counters);
+  int* seg_start = reinterpret_cast<int*>(base + L.seg_start);
+  uint32_t* seg_lb = reinterpret_cast<uint32_t*>(base + L.seg_lb);
+  int2* large = reinterpret_cast<int2*>(base + L.large);
+  int* tile_base = reinterpret_cast<int*>(base + L.tile_base);
+  int* tile_owner = reinterpret_cast<int*>(base + L.tile_owner);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(base + L.hist);
+  uint32_t* lbs[2] = {reinterpret_cast<uint32_t*>(base + L.lb0),
+                      reinterpret_cast<uint32_t*>(base + L.lb1)};
+
+  QSD_CUDA(cudaMemsetAsync(base, 0, L.counters + sizeof(int) * kNumCounters, st));
+  const bool has_vals = vals && vals->elem_bytes != 0;
+  // values follow the coordinates buffer for buffer (selectors may differ)
+  const int flipv = (!ext && has_vals) ? (vals->selector ^ coords->selector) : 0;
+  auto buf_src = [&](int idx) {
+    Src s;
+    s.c = coords->buf[idx];
+    s.v = has_vals ? vals->buf[idx ^ flipv] : nullptr;
+    s.stride = coords->stride;
+    s.idx = idx;
+    return s;
+  };
+  auto cols = [&](const Src& src, int dst) {
+    Cols c;
+    c.in = src.c;
+    c.vin = src.v;
+    c.in_stride = src.stride;
+    c.out = coords->buf[dst];
+    c.vout = has_vals ? vals->buf[dst ^ flipv] : nullptr;
+    c.out_stride = coords->stride;
+    c.order = plan->order;
+    c.vbytes = has_vals ? vals->elem_bytes : 0;
+    return c;
+  };
+  Src cur = ext ? *ext : buf_src(coords->selector);
+  const int64_t R = 4 * plan->order + (has_vals ? vals->elem_bytes : 0);  // bytes per entry
+  auto tag = [&](const char* k, int gi, int pass, int64_t entries, int64_t bpe,
+                 int complement = 0) {
+    ProfTag t;
+    t.kernel = k;
+    t.group = gi;
+    t.pass = pass;
+    t.entries = entries;
+    t.dev_entries = entries < 0 ? counters + kCntLargeEntries : nullptr;
+    t.complement = complement;
+    t.total = nnz;
+    t.bytes_per_entry = bpe;
+    return t;
+  };
+#define QSD_LAUNCH(TAG, CALL)                                     \
+  do {                                                            \
+    const int rec_ = prof_enabled() ? prof_begin((TAG), st) : -1; \
+    const cudaError_t e_ = (CALL);                                \
+    prof_end(rec_, st);                                           \
+    if (e_ != cudaSuccess) return QSD_ERR_CUDA;                   \
+  } while (0)
+  if (plan->opts.validate)
+    QSD_LAUNCH(tag("validate", -1, -1, nnz, 4 * plan->order),
+               launch_validate(cur.c, cur.stride, plan->order, plan->dims, plan->tau, nnz,
+                               status, st));
+  const int T = onesweep_tile();
+  const int C = plan->local_capacity;
+
+  for (int gi = 0; gi < plan->ngroups && nnz > 0; ++gi) {
+    const Group& g = plan->groups[gi];
+    if (g.npasses == 0) continue;
+    PassList pl;
+    pl.npasses = g.npasses;
+    for (int p = 0; p < g.npasses; ++p) pl.pass[p] = g.pass[p];
+    const int P = g.npasses;
+    const bool internal = cur.idx >= 0;
+
+    if (g.prefix_len == 0 && nnz <= C) {
+      const int F = internal ? cur.idx ^ 1 : 0;
+      QSD_LAUNCH(tag("local_sort", gi, -1, nnz, 2 * R),
+                 launch_local_sort(cols(cur, F), pl, nullptr, counters, 1, nnz, C, status, st));
+      cur = buf_src(F);
+      continue;
+    }
+    // F: the buffer the group ends in; pass p writes dst(p), the last one F.
+    const int F = internal ? cur.idx ^ (P & 1) : 0;
+    auto dst = [&](int p) { return F ^ ((P - 1 - p) & 1); };
+    QSD_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * kNumCounters, st));
+    LargeSegs ls;
+    std::memset(&ls, 0, sizeof(ls));
+    ls.nnz = nnz;
+    ls.counters = counters;
+    int max_tiles, max_large;
+    int64_t large_entries;  // -1: known on the device only
+    if (g.prefix_len == 0) {
+      ls.single = 1;
+      ls.single_tiles = (nnz + T - 1) / T;
+      max_tiles = ls.single_tiles;
+      max_large = 1;
+      large_entries = nnz;
+      QSD_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * P * kRadix, st));
+    } else {
+      const int32_t* pcols[kMaxOrder];
+      for (int i = 0; i < g.prefix_len; ++i)
+        pcols[i] = cur.c + (int64_t)g.prefix_modes[i] * cur.stride;
+      QSD_CUDA(cudaMemsetAsync(seg_lb, 0, sizeof(uint32_t) * seg_lookback_words(nnz), st));
+      QSD_LAUNCH(tag("seg_discover", gi, -1, nnz, 4 * g.prefix_len),
+                 launch_seg_discover(pcols, g.prefix_len, nnz, seg_start, seg_lb, counters,
+                                     status, st));
+      QSD_LAUNCH(tag("seg_classify", gi, -1, nnz, 0),
+                 launch_seg_classify(seg_start, counters, nnz, C, T, large, tile_base,
+                                     tile_owner, hist, P, st));
+      // small buckets: straight into F (in place when F is the input buffer)
+      QSD_LAUNCH(tag("local_sort", gi, -1, -1, 2 * R, 1),
+                 launch_local_sort(cols(cur, F), pl, seg_start, counters, 0, nnz, C, status,
+                                   st));
+      ls.single = 0;
+      ls.seg = large;
+      ls.tile_base = tile_base;
+      ls.tile_owner = tile_owner;
+      max_tiles = L.max_tiles;
+      max_large = L.max_large;
+      large_entries = -1;
+    }
+    // Global passes over the large buckets (or the whole tensor).
+    QSD_LAUNCH(tag("digit_hist", gi, -1, large_entries, 4 * g.nkeys),
+               launch_digit_hist(cols(cur, dst(0)), ls, pl, hist, lbs[0], max_tiles, status,
+                                 st));
+    QSD_LAUNCH(tag("digit_scan", gi, -1, large_entries, 0),
+               launch_digit_scan(ls, P, hist, max_large, st));
+    for (int p = 0; p < P; ++p) {
+      const Src in = p == 0 ? cur : buf_src(dst(p - 1));
+      uint32_t* lb_next = (p + 1 < P) ? lbs[(p + 1) & 1] : nullptr;
+      QSD_LAUNCH(tag("onesweep", gi, p, large_entries, 2 * R),
+                 launch_onesweep_pass(cols(in, dst(p)), ls, g.pass[p], p, P, hist,
+                                      lbs[p & 1], lb_next, counters + kCntPassTile + p,
+                                      max_tiles, status, st));
+    }
+    cur = buf_src(F);
+  }
+  if (cur.idx < 0) {  // no group moved anything: the caller wants a distinct copy
+    QSD_LAUNCH(tag("copy", -1, -1, nnz, 2 * R), launch_copy(cols(cur, 0), nnz, st));
+    cur = buf_src(0);
+  }
+#undef QSD_LAUNCH
+  QSD_CUDA(launch_fold_status(status, st));
+  coords->selector = cur.idx;
+  if (has_vals) vals->selector = cur.idx ^ flipv;
+  return QSD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qsd_status qsd_workspace_bytes(qsd_plan_t plan, int64_t nnz, size_t* bytes) {
+  if (!plan || !bytes || nnz < 0) return QSD_ERR_INVALID_ARGUMENT;
+  if (nnz > kMaxNnz) return QSD_ERR_UNSUPPORTED;
+  *bytes = layout_for(plan, nnz).total;
+  return QSD_OK;
+}
+
+qsd_status qsd_transpose_ws(qsd_coords* coords, qsd_values* vals, int64_t nnz,
+                            qsd_plan_t plan, void* workspace, size_t workspace_bytes,
+                            void* stream) {
+  qsd_status s = check_buffers(coords, vals, nnz, plan);
+  if (s != QSD_OK) return s;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & (kAlign - 1)))
+    return QSD_ERR_INVALID_ARGUMENT;
+  const Layout L = layout_for(plan, nnz);
+  if (workspace_bytes < L.total) return QSD_ERR_WORKSPACE_TOO_SMALL;
+  return run_plan(coords, vals, nullptr, nnz, plan, workspace, L, (cudaStream_t)stream);
+}
+
+qsd_status qsd_transpose_from_ws(const int32_t* in_coords, int64_t in_stride,
+                                 const void* in_vals, qsd_coords* out_coords,
+                                 qsd_values* out_vals, int64_t nnz, qsd_plan_t plan,
+                                 void* workspace, size_t workspace_bytes, void* stream) {
+  qsd_status s = check_buffers(out_coords, out_vals, nnz, plan);
+  if (s != QSD_OK) return s;
+  const bool has_vals = out_vals && out_vals->elem_bytes != 0;
+  if (nnz > 0 && (!in_coords || in_stride < nnz)) return QSD_ERR_INVALID_ARGUMENT;
+  if (has_vals && nnz > 0 && !in_vals) return QSD_ERR_INVALID_ARGUMENT;
+  if (nnz > 0 && (in_coords == out_coords->buf[0] || in_coords == out_coords->buf[1]))
+    return QSD_ERR_INVALID_ARGUMENT;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & (kAlign - 1)))
+    return QSD_ERR_INVALID_ARGUMENT;
+  const Layout L = layout_for(plan, nnz);
+  if (workspace_bytes < L.total) return QSD_ERR_WORKSPACE_TOO_SMALL;
+  Src ext;
+  ext.c = in_coords;
+  ext.v = has_vals ? in_vals : nullptr;
+  ext.stride = in_stride;
+  ext.idx = -1;
+  if (nnz == 0) {
+    out_coords->selector = 0;
+    if (has_vals) out_vals->selector = 0;
+  }
+  return run_plan(out_coords, out_vals, nnz > 0 ? &ext : nullptr, nnz, plan, workspace, L,
+                  (cudaStream_t)stream);
+}
+
+qsd_status qsd_transpose(qsd_coords* coords, qsd_values* vals, int64_t nnz,
+                         qsd_plan_t plan, void* stream) {
+  qsd_status s = check_buffers(coords, vals, nnz, plan);
+  if (s != QSD_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Layout L = layout_for(plan, nnz);
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, L.total, st) != cudaSuccess) {
+    cudaGetLastError();
+    return QSD_ERR_OUT_OF_MEMORY;
+  }
+  s = run_plan(coords, vals, nullptr, nnz, plan, ws, L, st);
+  if (cudaFreeAsync(ws, st) != cudaSuccess && s == QSD_OK) s = QSD_ERR_CUDA;
+  return s;
+}
+
+qsd_status qsd_transpose_host(const int32_t* host_coords, int64_t host_stride,
+                              const void* host_vals, int32_t* host_out_coords,
+                              int64_t host_out_stride, void* host_out_vals, int64_t nnz,
+                              qsd_plan_t plan, qsd_coords* dev_coords,
+                              qsd_values* dev_vals, void* workspace,
+                              size_t workspace_bytes, void* stream) {
+  qsd_status s = check_buffers(dev_coords, dev_vals, nnz, plan);
+  if (s != QSD_OK) return s;
+  const bool has_vals = dev_vals && dev_vals->elem_bytes != 0;
+  if (nnz > 0 && (!host_coords || !host_out_coords)) return QSD_ERR_INVALID_ARGUMENT;
+  if (host_stride < nnz || host_out_stride < nnz) return QSD_ERR_INVALID_ARGUMENT;
+  if (has_vals && nnz > 0 && (!host_vals || !host_out_vals)) return QSD_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int r = plan->order;
+  if (nnz > 0) {
+    QSD_CUDA(cudaMemcpy2DAsync(dev_coords->buf[dev_coords->selector],
+                               sizeof(int32_t) * dev_coords->stride, host_coords,
+                               sizeof(int32_t) * host_stride, sizeof(int32_t) * nnz, r,
+                               cudaMemcpyHostToDevice, st));
+    if (has_vals)
+      QSD_CUDA(cudaMemcpyAsync(dev_vals->buf[dev_vals->selector], host_vals,
+                               (size_t)dev_vals->elem_bytes * nnz, cudaMemcpyHostToDevice,
+                               st));
+  }
+  s = qsd_transpose_ws(dev_coords, dev_vals, nnz, plan, workspace, workspace_bytes, stream);
+  if (s != QSD_OK) return s;
+  if (nnz > 0) {
+    QSD_CUDA(cudaMemcpy2DAsync(host_out_coords, sizeof(int32_t) * host_out_stride,
+                               dev_coords->buf[dev_coords->selector],
+                               sizeof(int32_t) * dev_coords->stride, sizeof(int32_t) * nnz,
+                               r, cudaMemcpyDeviceToHost, st));
+    if (has_vals)
+      QSD_CUDA(cudaMemcpyAsync(host_out_vals, dev_vals->buf[dev_vals->selector],
+                               (size_t)dev_vals->elem_bytes * nnz, cudaMemcpyDeviceToHost,
+                               st));
+  }
+  qsd_status dev_status = QSD_OK;
+  s = qsd_workspace_status(workspace, stream, &dev_status);
+  if (s != QSD_OK) return s;
+  return dev_status;
+}
+
+qsd_status qsd_workspace_status(const void* workspace, void* stream, qsd_status* out) {
+  if (!workspace || !out) return QSD_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned v = 0;
+  QSD_CUDA(cudaMemcpyAsync(&v, workspace, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  QSD_CUDA(cudaStreamSynchronize(st));
+  *out = (qsd_status)v;
+  return QSD_OK;
+}
+
+qsd_status qsd_get_async_status(void* stream, qsd_status* out) {
+  if (!out) return QSD_ERR_INVALID_ARGUMENT;
+  unsigned v = 0;
+  QSD_CUDA(qsd::read_and_clear_sticky(&v, (cudaStream_t)stream));
+  *out = (qsd_status)v;
+  return QSD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+"""Host-side tests of the C library (no GPU needed): every symbol declared in
+include/qsd.h is exported, argument errors are reported synchronously, and
+the planner behind qsd_plan matches the oracle planner call for call."""
+import ctypes
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2005_10427_gb300 as qsd
+from paper_2005_10427_gb300 import _capi
+from oracle import plan as OP
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    qsd.build()
+    return qsd.lib()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "qsd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qsd_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(L):
+    syms = declared_symbols()
+    assert len(syms) >= 12
+    for s in syms:
+        assert hasattr(L, s), s
+    assert {n for n, _, _ in _capi.SIGNATURES} == set(syms)
+    assert L.qsd_version().decode().startswith("qsd")
+
+
+def test_status_strings(L):
+    for code, name in _capi.STATUS_NAMES.items():
+        assert L.qsd_status_string(code).decode() == name
+
+
+def test_plan_argument_errors(L):
+    with pytest.raises(qsd.QsdError) as e:
+        qsd.Plan([4, 4, 4], [0, 0, 1])
+    assert e.value.status == 1
+    with pytest.raises(qsd.QsdError):
+        qsd.Plan([4, 0, 4], [2, 1, 0])
+    with pytest.raises(qsd.QsdError):
+        qsd.Plan([4, 4, 4], [2, 1, 0], input_mode_order=[0, 1, 1])
+    with pytest.raises(qsd.QsdError) as e:
+        qsd.Plan([2] * 9, list(range(9)))
+    assert e.value.status == 2
+    with pytest.raises(qsd.QsdError):
+        qsd.Plan([4, 4], [1, 0], digit_bits=9)
+    with pytest.raises(qsd.QsdError):
+        qsd.Plan([4, 4], [1, 0], local_capacity=3000)
+
+
+def test_transpose_argument_errors_without_gpu(L):
+    p = qsd.Plan([4, 4], [1, 0])
+    c = _capi.Coords()
+    c.stride = 10
+    c.selector = 0
+    # null buffers with nnz > 0
+    st = L.qsd_transpose_ws(ctypes.byref(c), None, 10, p.handle, None, 0, None)
+    assert st == 1
+    c.selector = 2
+    assert L.qsd_transpose_ws(ctypes.byref(c), None, 0, p.handle, None, 0, None) == 1
+    c.selector = 0
+    assert L.qsd_transpose_ws(ctypes.byref(c), None, -1, p.handle, None, 0, None) == 1
+    assert L.qsd_transpose_ws(ctypes.byref(c), None, 1 << 30, p.handle, None, 0, None) == 2
+    out = ctypes.c_size_t()
+    assert L.qsd_workspace_bytes(p.handle, -5, ctypes.byref(out)) == 1
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 4, 5])
+def test_planner_matches_oracle_planner(L, r):
+    rng = np.random.default_rng(r)
+    taus = [tuple(range(r))] + [tuple(int(x) for x in rng.permutation(r)) for _ in range(2)]
+    for tau in taus:
+        for sigma in itertools.permutations(range(r)):
+            p = qsd.Plan([7] * r, sigma, input_mode_order=tau)
+            inf = p.info()
+            want = OP.quesadilla_calls(sigma, tau)
+            assert inf["calls"] == want, (tau, sigma)
+            assert inf["num_calls"] == OP.b(tau, sigma)
+            assert inf["num_bucketed_calls"] == sum(1 for pre, _ in want if pre)
+            # groups: consecutive calls sharing a prefix, keys most significant first
+            groups = []
+            for pre, mode in want:
+                if groups and groups[-1][0] == pre:
+                    groups[-1][1].insert(0, mode)
+                else:
+                    groups.append((pre, [mode]))
+            assert [(g["prefix"], g["keys"]) for g in inf["groups"]] == \
+                [(pre, tuple(k)) for pre, k in groups]
+
+
+def test_planner_high_order_sampled(L):
+    rng = np.random.default_rng(99)
+    for r in (6, 7, 8):
+        for _ in range(40):
+            tau = tuple(int(x) for x in rng.permutation(r))
+            sigma = tuple(int(x) for x in rng.permutation(r))
+            assert qsd.Plan([3] * r, sigma, input_mode_order=tau).calls == \
+                OP.quesadilla_calls(sigma, tau)
+
+
+def test_fig4_through_the_c_abi(L):
+    for r, want in ((3, [1, 3, 2]), (4, [1, 6, 11, 6]), (5, [1, 10, 35, 50, 24])):
+        hist = [0] * r
+        for sigma in itertools.permutations(range(r)):
+            hist[qsd.Plan([5] * r, sigma).info()["num_calls"]] += 1
+        assert hist == want
+
+
+def test_key_bits_and_digit_passes(L):
+    # 12000 x 9000 x 28000: widths 14, 14, 15
+    cases = {(0, 2, 1): [((0,), (2,), 15)], (1, 0, 2): [((), (1,), 14)],
+             (1, 2, 0): [((), (1, 2), 29)], (2, 1, 0): [((), (2, 1), 29)],
+             (2, 0, 1): [((), (2,), 15)]}
+    for sigma, want in cases.items():
+        inf = qsd.Plan([12000, 9000, 28000], sigma).info()
+        got = [(g["prefix"], g["keys"], g["key_bits"]) for g in inf["groups"]]
+        assert got == want
+        for g in inf["groups"]:
+            assert g["passes"] == -(-g["key_bits"] // 8)
+    inf = qsd.Plan([4_800_000, 1_700_000, 1_800_000, 1100], (1, 0, 3, 2)).info()
+    assert [(g["prefix"], g["keys"], g["key_bits"]) for g in inf["groups"]] == \
+        [((), (1,), 21), ((1, 0), (3,), 11)]
+    inf = qsd.Plan([4_800_000, 1_700_000, 1_800_000, 1100], (3, 2, 1, 0)).info()
+    assert inf["groups"][0]["key_bits"] == 11 + 21 + 21 and inf["groups"][0]["passes"] == 7
+    # modes of size 1 contribute no bits; a key of only such modes needs no pass
+    inf = qsd.Plan([1, 5, 1], (2, 0, 1)).info()
+    assert inf["groups"][0]["key_bits"] == 0 and inf["groups"][0]["passes"] == 0
+    inf = qsd.Plan([5, 5], (1, 0), digit_bits=1).info()
+    assert inf["groups"][0]["passes"] == 3
+
+
+def test_no_skip_plan_is_full_radix(L):
+    inf = qsd.Plan([10, 10, 10, 10], (0, 1, 2, 3), no_skip=True).info()
+    assert inf["num_calls"] == 4 and inf["groups"][0]["keys"] == (0, 1, 2, 3)
+    assert qsd.Plan([10, 10, 10, 10], (0, 1, 2, 3)).info()["num_calls"] == 0
+
+
+def test_workspace_bytes(L):
+    p = qsd.Plan([12000, 9000, 28000], (0, 2, 1))
+    small, big = p.workspace_bytes(1000), p.workspace_bytes(76_000_000)
+    assert 0 < small < big < 76_000_000 * 16
+    assert p.workspace_bytes(0) > 0

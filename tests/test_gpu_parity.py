@@ -1,0 +1,235 @@
+"""GPU parity: the CUDA path, called through the C ABI, must equal the CPU
+oracle (a stable sort under the target-order lexicographic comparator) bit
+for bit in coordinates and values. Values are moved, never computed, so the
+tolerance is zero."""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qsd():
+    import paper_2005_10427_gb300 as q
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    q.build()
+    q.lib()
+    return q
+
+
+def run_gpu(qsd, coords, vals, dims, sigma, tau=None, **opts):
+    plan = qsd.Plan(dims, sigma, input_mode_order=tau, **opts)
+    c = torch.from_numpy(np.ascontiguousarray(coords)).cuda()
+    v = None if vals is None else torch.from_numpy(np.ascontiguousarray(vals)).cuda()
+    oc, ov = qsd.transpose(c, v, plan)
+    torch.cuda.synchronize()
+    assert qsd.get_async_status() == 0
+    return oc.cpu().numpy(), (None if ov is None else ov.cpu().numpy())
+
+
+def check(qsd, coords, vals, dims, sigma, tau=None, **opts):
+    gc, gv = run_gpu(qsd, coords, vals, dims, sigma, tau, **opts)
+    rc, rv = oracle.transpose(coords, vals, sigma)
+    assert gc.shape == rc.shape
+    bad = np.nonzero(np.any(gc != rc, axis=0))[0]
+    assert bad.size == 0, f"sigma={sigma} first mismatch at {bad[:5]} of {rc.shape[1]}"
+    if vals is not None:
+        u = np.uint64 if vals.dtype.itemsize == 8 else np.uint32
+        assert np.array_equal(gv.view(u), rv.view(u)), f"values differ for sigma={sigma}"
+
+
+def tensor(dims, nnz, seed, val_kind="f32_normal", zipf=0.0, dup=0.0, tau=None):
+    t = synth.random_coo(dims, nnz, seed, val_kind, zipf=zipf, dup_frac=dup, input_order=tau)
+    return t.coords.numpy(), t.vals.numpy()
+
+
+@pytest.mark.parametrize("r", [2, 3, 4])
+def test_small_all_permutations(qsd, r):
+    dims = [13, 7, 29, 5][:r]
+    coords, vals = tensor(dims, 900, seed=r, dup=0.2)
+    for sigma in itertools.permutations(range(r)):
+        check(qsd, coords, vals, dims, sigma)
+
+
+@pytest.mark.parametrize("nnz", [0, 1, 2, 31, 32, 33, 1023, 1024, 1025, 4095, 4096, 4097,
+                                 8191, 8192, 8193, 20000])
+def test_sizes_and_ragged_tails(qsd, nnz):
+    dims = [60, 50, 70]
+    coords, vals = tensor(dims, nnz, seed=nnz + 3, zipf=1.1) if nnz else \
+        (np.zeros((3, 0), np.int32), np.zeros(0, np.float32))
+    for sigma in [(0, 2, 1), (2, 1, 0), (1, 0, 2)]:
+        check(qsd, coords, vals, dims, sigma)
+
+
+def test_global_multi_tile_and_large_buckets(qsd):
+    # Zipf heads give buckets far above the shared-memory capacity, so both the
+    # block-local sort and the segmented digit passes run in one group.
+    dims = [300, 2000, 3000]
+    coords, vals = tensor(dims, 400_000, seed=11, zipf=1.1)
+    for sigma in itertools.permutations(range(3)):
+        check(qsd, coords, vals, dims, sigma)
+
+
+@pytest.mark.parametrize("val_kind", ["f32_normal", "f64_uniform", None])
+def test_value_widths(qsd, val_kind):
+    dims = [100, 80, 90]
+    coords, vals = tensor(dims, 50_000, seed=5, val_kind=val_kind or "f32_normal", zipf=1.2)
+    if val_kind is None:
+        vals = None
+    for sigma in [(0, 2, 1), (1, 2, 0)]:
+        check(qsd, coords, vals, dims, sigma)
+
+
+def test_payload_bits_preserved(qsd):
+    dims = [50, 40, 30]
+    coords, _ = tensor(dims, 30_000, seed=8, zipf=1.0)
+    rng = np.random.default_rng(0)
+    raw = rng.integers(0, 2**63, size=coords.shape[1], dtype=np.uint64)
+    raw[::7] = 0x7FF8000000000001  # NaN payload
+    raw[1::7] = 0x8000000000000000  # -0.0
+    check(qsd, coords, raw.view(np.float64), dims, (2, 0, 1))
+    raw32 = (raw & 0xFFFFFFFF).astype(np.uint32)
+    check(qsd, coords, raw32.view(np.float32), dims, (1, 0, 2))
+
+
+def test_duplicates_are_stable(qsd):
+    dims = [6, 5, 7, 4]
+    coords, vals = tensor(dims, 600, seed=21, dup=3.0)
+    assert coords.shape[1] > 600
+    for sigma in itertools.permutations(range(4)):
+        check(qsd, coords, vals, dims, sigma)
+    # many duplicates across several tiles and buckets
+    coords, vals = tensor([40, 30, 20], 20_000, seed=22, zipf=1.3, dup=1.5)
+    for sigma in [(0, 2, 1), (2, 1, 0)]:
+        check(qsd, coords, vals, [40, 30, 20], sigma)
+
+
+def test_non_identity_input_order(qsd):
+    dims = [70, 40, 90, 11]
+    for tau in [(2, 0, 3, 1), (3, 2, 1, 0)]:
+        coords, vals = tensor(dims, 30_000, seed=31, zipf=1.1, tau=tau)
+        rng = np.random.default_rng(1)
+        for sigma in [tuple(int(x) for x in rng.permutation(4)) for _ in range(6)]:
+            check(qsd, coords, vals, dims, sigma, tau=tau)
+
+
+def test_wide_keys_over_32_and_64_bits(qsd):
+    dims = [1 << 20, 1 << 21, 1 << 22, 1 << 20, 1 << 19]  # 102 packed bits
+    coords, vals = tensor(dims, 60_000, seed=41, val_kind="f64_normal", zipf=1.05)
+    for sigma in [(4, 3, 2, 1, 0), (2, 4, 0, 1, 3), (0, 4, 3, 2, 1), (1, 0, 4, 3, 2)]:
+        check(qsd, coords, vals, dims, sigma)
+
+
+def test_unit_modes_and_degenerate_keys(qsd):
+    dims = [1, 9, 1, 7]
+    coords, vals = tensor(dims, 50, seed=3)
+    for sigma in itertools.permutations(range(4)):
+        check(qsd, coords, vals, dims, sigma)
+    # one giant bucket: every entry shares the prefix coordinate
+    dims = [1, 500, 400]
+    coords, vals = tensor(dims, 60_000, seed=4, zipf=0.8)
+    check(qsd, coords, vals, dims, (0, 2, 1))
+    # every bucket has one entry
+    dims = [70_000, 3, 3]
+    c = np.stack([np.arange(70_000), np.arange(70_000) % 3, np.arange(70_000) % 2]).astype(np.int32)
+    check(qsd, c, np.arange(70_000, dtype=np.float32), dims, (0, 2, 1))
+
+
+@pytest.mark.parametrize("digit_bits", [1, 3, 5, 7, 8])
+def test_digit_widths(qsd, digit_bits):
+    dims = [200, 300, 400]
+    coords, vals = tensor(dims, 100_000, seed=50 + digit_bits, zipf=1.1)
+    for sigma in [(0, 2, 1), (2, 0, 1)]:
+        check(qsd, coords, vals, dims, sigma, digit_bits=digit_bits)
+
+
+@pytest.mark.parametrize("cap", [1024, 2048, 4096, 8192])
+def test_local_capacities(qsd, cap):
+    dims = [3000, 500, 700]
+    coords, vals = tensor(dims, 200_000, seed=60, zipf=1.1)
+    for sigma in [(0, 2, 1), (0, 1, 2), (1, 0, 2)]:
+        check(qsd, coords, vals, dims, sigma, local_capacity=cap)
+
+
+def test_no_skip_plan(qsd):
+    dims = [50, 60, 70]
+    coords, vals = tensor(dims, 40_000, seed=70, zipf=1.1)
+    for sigma in [(0, 1, 2), (0, 2, 1), (2, 1, 0)]:
+        check(qsd, coords, vals, dims, sigma, no_skip=True)
+
+
+def test_validate_reports_bad_input(qsd):
+    dims = [10, 10, 10]
+    coords, vals = tensor(dims, 500, seed=1)
+    plan = qsd.Plan(dims, (2, 1, 0), validate=True)
+    c = torch.from_numpy(coords).cuda()
+    qsd.transpose(c, torch.from_numpy(vals).cuda(), plan)
+    assert qsd.get_async_status() == 0
+    bad = coords.copy()
+    bad[:, [10, 400]] = bad[:, [400, 10]]  # breaks the input order
+    qsd.transpose(torch.from_numpy(bad).cuda(), torch.from_numpy(vals).cuda(), plan)
+    assert qsd.get_async_status() == 5
+    oob = coords.copy()
+    oob[1, 7] = 10
+    qsd.transpose(torch.from_numpy(oob).cuda(), torch.from_numpy(vals).cuda(), plan)
+    assert qsd.get_async_status() == 6
+    assert qsd.get_async_status() == 0  # read clears
+
+
+def test_transpose_host_end_to_end(qsd):
+    dims = [300, 200, 100]
+    coords, vals = tensor(dims, 120_000, seed=80, zipf=1.1)
+    plan = qsd.Plan(dims, (2, 0, 1))
+    n = coords.shape[1]
+    hc = torch.from_numpy(coords).pin_memory()
+    hv = torch.from_numpy(vals).pin_memory()
+    oc = torch.empty_like(hc).pin_memory()
+    ov = torch.empty_like(hv).pin_memory()
+    cb = [torch.empty((3, n), dtype=torch.int32, device="cuda") for _ in range(2)]
+    vb = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(2)]
+    ws = torch.empty(plan.workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    qsd.transpose_host(hc, hv, plan, cb, vb, ws, oc, ov)
+    rc, rv = oracle.transpose(coords, vals, (2, 0, 1))
+    assert np.array_equal(oc.numpy(), rc) and np.array_equal(ov.numpy(), rv)
+
+
+def test_repeated_calls_reuse_workspace(qsd):
+    dims = [500, 400, 300]
+    coords, vals = tensor(dims, 150_000, seed=90, zipf=1.1)
+    plan = qsd.Plan(dims, (0, 2, 1))
+    n = coords.shape[1]
+    ws = torch.empty(plan.workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    rc, rv = oracle.transpose(coords, vals, (0, 2, 1))
+    for _ in range(3):
+        cb = [torch.from_numpy(coords).cuda(), torch.empty((3, n), dtype=torch.int32, device="cuda")]
+        vb = [torch.from_numpy(vals).cuda(), torch.empty(n, dtype=torch.float32, device="cuda")]
+        sel = qsd.transpose_buffers(cb, vb, 0, n, plan, ws)
+        assert qsd.workspace_status(ws) == 0
+        assert np.array_equal(cb[sel].cpu().numpy(), rc)
+        assert np.array_equal(vb[sel].cpu().numpy(), rv)
+
+
+def test_out_of_place_keeps_input(qsd):
+    dims = [400, 300, 200]
+    coords, vals = tensor(dims, 100_000, seed=95, zipf=1.1)
+    n = coords.shape[1]
+    ic = torch.from_numpy(coords).cuda()
+    iv = torch.from_numpy(vals).cuda()
+    cb = [torch.empty((3, n), dtype=torch.int32, device="cuda") for _ in range(2)]
+    vb = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(2)]
+    for sigma in [(0, 1, 2), (0, 2, 1), (1, 0, 2), (2, 1, 0), (1, 2, 0)]:
+        plan = qsd.Plan(dims, sigma)
+        ws = torch.empty(plan.workspace_bytes(n), dtype=torch.uint8, device="cuda")
+        sel = qsd.transpose_from(ic, iv, cb, vb, n, plan, ws)
+        assert qsd.workspace_status(ws) == 0
+        rc, rv = oracle.transpose(coords, vals, sigma)
+        assert np.array_equal(cb[sel].cpu().numpy(), rc), sigma
+        assert np.array_equal(vb[sel].cpu().numpy(), rv), sigma
+        assert np.array_equal(ic.cpu().numpy(), coords) and np.array_equal(iv.cpu().numpy(), vals)
