@@ -64,6 +64,82 @@ __device__ __forceinline__ uint32_t wait_flag(const uint32_t* p, unsigned* statu
   }
 }
 
+// As wait_flag, but reports whether the word was published (false: timed out,
+// status recorded).
+__device__ __forceinline__ bool wait_flag_ok(const uint32_t* p, unsigned* status) {
+  if (ld_relaxed(p) & kLbStateMask) return true;
+  uint64_t t0 = global_timer_ns();
+  unsigned spins = 0;
+  while (!(ld_relaxed(p) & kLbStateMask)) {
+    if ((++spins & 63u) == 0) {
+      if (global_timer_ns() - t0 > kSpinLimitNs) {
+        set_status(status, QSD_ERR_TIMEOUT);
+        return false;
+      }
+      __nanosleep(32);
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA engine, non-tensor form) into shared memory,
+// completed on an mbarrier. Addresses and sizes must be multiples of 16 B.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// One arrival that also announces `bytes` of incoming transactions.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// A plain arrival (no transaction count).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+      "selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity to complete. Returns false
+// (and records QSD_ERR_TIMEOUT) if it did not within kSpinLimitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_timer_ns() - t0 > kSpinLimitNs) {
+      set_status(status, QSD_ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Radix digit of one entry for one pass: OR of bit slices of its coordinates.
 __device__ __forceinline__ uint32_t field_bits(uint32_t c, const DigitField& f) {
@@ -80,31 +156,56 @@ __device__ __forceinline__ uint32_t field_bits(uint32_t c, const DigitField& f) 
 // by digit; s_bin_start[d] / s_bin_count[d] give each digit's run.
 // Ranking inside a round uses __match_any_sync (lanes with equal digits) and
 // a per-warp running count in shared memory.
-template <int NWARPS, int ITEMS>
+// Barrier over the first NTHREADS threads: the whole block when BAR == 0,
+// else named barrier BAR.
+template <int BAR, int NTHREADS>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (BAR == 0) {
+    __syncthreads();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NTHREADS) : "memory");
+  }
+}
+
+// Counts fit 16 bits (a tile has at most 65535 entries). With BAR != 0 the
+// ranking threads are the first NWARPS warps of the block and synchronise on
+// named barrier BAR only (other warps of the block may be doing other work).
+template <int NWARPS, int ITEMS, int BAR = 0>
 __device__ __forceinline__ void block_rank(const uint32_t (&dig)[ITEMS],
                                            uint32_t (&rank)[ITEMS],
-                                           uint32_t* s_warp_hist,  // [NWARPS][kRadix]
+                                           uint16_t* s_warp_hist,  // [NWARPS][kRadix]
                                            uint32_t* s_bin_start,  // [kRadix]
                                            uint32_t* s_bin_count)  // [kRadix]
 {
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
-  uint32_t* h = s_warp_hist + w * kRadix;
+  uint16_t* h = s_warp_hist + w * kRadix;
+  // the warp's 16-bit counters, two digits per 32-bit word
+  uint32_t* h32 = reinterpret_cast<uint32_t*>(h);
 #pragma unroll
-  for (int d = lane; d < kRadix; d += 32) h[d] = 0;
+  for (int k = lane; k < kRadix / 2; k += 32) h32[k] = 0;
   __syncwarp();
   const uint32_t lt = (1u << lane) - 1u;
+  // lanes with equal digits, for every round at once
+  uint32_t peers[ITEMS];
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) peers[i] = __match_any_sync(0xffffffffu, dig[i]);
+  // one leader per digit and round adds the round's count to the warp's
+  // counter; shared atomics of one warp to one address apply in issue order,
+  // so each round sees the counts of the rounds before it
+  uint32_t old[ITEMS];
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
-    const uint32_t d = dig[i];
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t pre = h[d];
-    rank[i] = pre + __popc(peers & lt);
-    __syncwarp();
-    if (lane == __ffs(peers) - 1) h[d] = pre + __popc(peers);
-    __syncwarp();
+    old[i] = 0;
+    if (lane == __ffs(peers[i]) - 1)
+      old[i] = atomicAdd(&h32[dig[i] >> 1], (uint32_t)__popc(peers[i]) << ((dig[i] & 1u) * 16));
   }
-  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t o = __shfl_sync(0xffffffffu, old[i], __ffs(peers[i]) - 1);
+    rank[i] = ((o >> ((dig[i] & 1u) * 16)) & 0xffffu) + __popc(peers[i] & lt);
+  }
+  group_sync<BAR, NWARPS * 32>();
   // exclusive scan over warps for each digit; digit totals
   for (int d = threadIdx.x; d < kRadix; d += NWARPS * 32) {
     uint32_t run = 0;
@@ -116,7 +217,7 @@ __device__ __forceinline__ void block_rank(const uint32_t (&dig)[ITEMS],
     }
     s_bin_count[d] = run;
   }
-  __syncthreads();
+  group_sync<BAR, NWARPS * 32>();
   // exclusive scan over digits (one warp, kRadix/32 digits per lane)
   if (w == 0) {
     constexpr int PER = kRadix / 32;
@@ -140,7 +241,7 @@ __device__ __forceinline__ void block_rank(const uint32_t (&dig)[ITEMS],
       run += v[j];
     }
   }
-  __syncthreads();
+  group_sync<BAR, NWARPS * 32>();
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i)
     rank[i] += s_bin_start[dig[i]] + h[dig[i]];

@@ -1,0 +1,587 @@
+// Global stable radix passes for buckets too large for one thread block
+// (and for the whole tensor when a group has no prefix).
+//
+// A pass is the GPU form of one histogram partial sort (Algorithm 1: count,
+// prefix-sum, stable move) over a radix digit of the packed key instead of a
+// whole mode, so the count array has at most 2^8 bins rather than n_k (the
+// cost the paper's discussion attributes to large modes). The count and the
+// prefix sum are done per chunk (a run of consecutive entries inside one
+// bucket), which makes the move free of any dependency between thread
+// blocks:
+//   k_chunk_hist   per chunk: histogram of the pass's digit (one read of the
+//                  key coordinates the digit comes from); per chunk group:
+//                  the sum of its chunks' histograms;
+//   k_chunk_scan   per chunk group: every chunk's first output slot for each
+//                  digit = bucket start + entries of smaller digits in the
+//                  bucket + entries of the same digit in earlier chunks;
+//   k_digit_move   per chunk (claimed dynamically): tiles of the chunk are
+//                  staged in shared memory by bulk asynchronous copies (the
+//                  next tile's copies overlap the current tile), ranked
+//                  stably by digit, and every row is written through the
+//                  inverse permutation to the chunk's running slots.
+// Buckets never exchange entries (Section 3.2: coordinates do not leave
+// their bucket), so offsets are computed per bucket.
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <type_traits>
+
+#include "device_common.cuh"
+#include "kernels.cuh"
+
+namespace qsd {
+
+namespace {
+
+constexpr int kHistThreads = 256;
+constexpr int kHistWarps = kHistThreads / 32;
+constexpr int kHistRun = 8;  // consecutive entries per thread
+constexpr int kMaxRows = kMaxOrder + 1;
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+__device__ __forceinline__ int n_chunks(const LargeSegs& ls) {
+  return ls.single ? (ls.nnz + ls.chunk - 1) / ls.chunk : ls.counters[kCntNumChunks];
+}
+__device__ __forceinline__ int n_groups(const LargeSegs& ls) {
+  return ls.single ? (n_chunks(ls) + kGroupChunks - 1) / kGroupChunks
+                   : ls.counters[kCntNumGroups];
+}
+
+struct ChunkInfo {
+  int seg;     // large-bucket index
+  int start;   // first entry of the chunk
+  int end;     // one past its last entry
+  int group;   // its chunk group
+  int lo, hi;  // the bucket's entry range
+};
+
+__device__ __forceinline__ ChunkInfo chunk_info(const LargeSegs& ls, int c) {
+  ChunkInfo ci;
+  int s, cb, gb, lo, hi;
+  if (ls.single) {
+    s = 0;
+    cb = 0;
+    gb = 0;
+    lo = 0;
+    hi = ls.nnz;
+  } else {
+    s = ls.chunk_owner[c];
+    const int2 se = ls.seg[s];
+    cb = ls.chunk_base[s];
+    gb = ls.group_base[s];
+    lo = se.x;
+    hi = se.y;
+  }
+  const int lc = c - cb;
+  ci.seg = s;
+  ci.start = lo + lc * ls.chunk;
+  ci.end = min(ci.start + ls.chunk, hi);
+  ci.group = gb + lc / kGroupChunks;
+  ci.lo = lo;
+  ci.hi = hi;
+  return ci;
+}
+
+// ---------------------------------------------------------------------------
+// Chunk histograms. Each thread counts kHistRun consecutive entries into its
+// warp's histogram, one shared atomic per run of equal digits.
+__global__ void __launch_bounds__(kHistThreads)
+k_chunk_hist(Cols c, LargeSegs ls, PassDesc pd, uint32_t* __restrict__ chunk_hist,
+             uint32_t* __restrict__ group_sum, int* __restrict__ claim) {
+  __shared__ uint32_t s_hist[kHistWarps][kRadix];
+  __shared__ int s_chunk;
+  const int w = threadIdx.x >> 5;
+  const int nc = n_chunks(ls);
+  const int nbins = 1 << pd.bits;
+  while (true) {
+    for (int i = threadIdx.x; i < kHistWarps * kRadix; i += kHistThreads)
+      (&s_hist[0][0])[i] = 0;
+    if (threadIdx.x == 0) s_chunk = atomicAdd(claim, 1);
+    __syncthreads();
+    const int ch = s_chunk;
+    if (ch >= nc) break;
+    const ChunkInfo ci = chunk_info(ls, ch);
+    for (int base = ci.start + threadIdx.x * kHistRun; base < ci.end;
+         base += kHistThreads * kHistRun) {
+      const int n = min(kHistRun, ci.end - base);
+      uint32_t d[kHistRun];
+#pragma unroll
+      for (int k = 0; k < kHistRun; ++k) d[k] = 0;
+      for (int f = 0; f < pd.nfields; ++f) {
+        const DigitField fd = pd.f[f];
+        const int32_t* col = c.in + (int64_t)fd.mode * c.in_stride + base;
+        uint32_t v[kHistRun];
+#pragma unroll
+        for (int k = 0; k < kHistRun; ++k) v[k] = k < n ? (uint32_t)__ldg(col + k) : 0u;
+#pragma unroll
+        for (int k = 0; k < kHistRun; ++k) d[k] |= field_bits(v[k], fd);
+      }
+      uint32_t run_d = d[0], run_n = 1;
+#pragma unroll
+      for (int k = 1; k < kHistRun; ++k) {
+        if (k < n) {
+          if (d[k] == run_d) {
+            ++run_n;
+          } else {
+            atomicAdd(&s_hist[w][run_d], run_n);
+            run_d = d[k];
+            run_n = 1;
+          }
+        }
+      }
+      atomicAdd(&s_hist[w][run_d], run_n);
+    }
+    __syncthreads();
+    for (int dd = threadIdx.x; dd < nbins; dd += kHistThreads) {
+      uint32_t v = 0;
+#pragma unroll
+      for (int ww = 0; ww < kHistWarps; ++ww) v += s_hist[ww][dd];
+      chunk_hist[(size_t)ch * kRadix + dd] = v;
+      if (v) atomicAdd(group_sum + (size_t)ci.group * kRadix + dd, v);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Chunk offsets. One block (kRadix threads, one per digit) per chunk group.
+__global__ void __launch_bounds__(kRadix)
+k_chunk_scan(LargeSegs ls, uint32_t* __restrict__ chunk_hist,
+             const uint32_t* __restrict__ group_sum) {
+  __shared__ uint32_t s_tmp[kRadix / 32 + 1];
+  const int d = threadIdx.x;
+  const int ng_all = n_groups(ls);
+  const int nc_all = n_chunks(ls);
+  for (int G = blockIdx.x; G < ng_all; G += gridDim.x) {
+    int s, gb, cb, ng, nc, lo;
+    if (ls.single) {
+      s = 0;
+      gb = 0;
+      cb = 0;
+      ng = ng_all;
+      nc = nc_all;
+      lo = 0;
+    } else {
+      s = ls.group_owner[G];
+      const int2 se = ls.seg[s];
+      gb = ls.group_base[s];
+      cb = ls.chunk_base[s];
+      nc = (se.y - se.x + ls.chunk - 1) / ls.chunk;
+      ng = (nc + kGroupChunks - 1) / kGroupChunks;
+      lo = se.x;
+    }
+    (void)s;
+    // bucket total and the sum over the bucket's earlier groups, per digit
+    uint32_t total = 0, prior = 0;
+    for (int g = gb; g < gb + ng; ++g) {
+      const uint32_t v = group_sum[(size_t)g * kRadix + d];
+      total += v;
+      if (g < G) prior += v;
+    }
+    uint32_t tot_all;
+    const uint32_t below = block_exclusive_sum<kRadix / 32>(total, s_tmp, &tot_all);
+    uint32_t off = (uint32_t)lo + below + prior;
+    const int c0 = cb + (G - gb) * kGroupChunks;
+    const int c1 = min(c0 + kGroupChunks, cb + nc);
+    for (int c = c0; c < c1; c += 8) {
+      uint32_t h[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) h[k] = c + k < c1 ? chunk_hist[(size_t)(c + k) * kRadix + d] : 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (c + k < c1) {
+          chunk_hist[(size_t)(c + k) * kRadix + d] = off;
+          off += h[k];
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The move, warp-specialised. One block per SM runs a three-role pipeline
+// over the tiles of the chunks it claims:
+//   producer (1 warp)  claims chunks, describes each tile in a ring slot,
+//                      loads its rows' unaligned edges and starts bulk
+//                      copies of the aligned bodies into the slot's staging
+//                      buffer (NS slots);
+//   rankers (8 warps)  compute the digits of tile k+1, rank them stably and
+//                      turn the chunk's running output slots into each
+//                      sorted position's destination;
+//   writers (8 warps)  write tile k's rows through the inverse permutation.
+// Ranking and writing overlap, and the copies run NS-1 tiles ahead, so
+// neither the ranking latency nor the load latency is on the critical path.
+// Hand-offs use mbarriers (every wait bounded); the rankers synchronise
+// among themselves on named barrier 1.
+
+constexpr int kWsRankWarps = 8;
+constexpr int kWsWriteWarps = 8;
+constexpr int kWsRankThreads = kWsRankWarps * 32;
+constexpr int kWsWriteThreads = kWsWriteWarps * 32;
+constexpr int kWsThreads = kWsRankThreads + kWsWriteThreads + 32;  // + producer warp
+
+// Where one row of a tile lands in its shared-memory slot: entry i is at
+// byte off + i * esz; entries [0, head) and [tail_from, n) arrive by plain
+// loads, the 16-byte-aligned body between them by one bulk copy.
+struct RowPlan {
+  int off;
+  int head;
+  int tail_from;
+};
+
+// One unit of work: tile `k` of chunk `chunk` (chunk >= nchunks: the end).
+struct TileSlot {
+  int chunk, k, ntile, start, end, lo, hi;
+  RowPlan row[kMaxRows];
+};
+
+template <int T, int NS>
+struct WsShared {
+  uint64_t full[NS];     // producer -> rankers: tile staged
+  uint64_t empty[NS];    // writers -> producer: staging buffer free
+  uint64_t ranked[2];    // rankers -> writers: destinations ready
+  uint64_t consumed[2];  // writers -> rankers: destinations used
+  TileSlot slot[NS];
+  uint32_t off[kRadix];  // rankers: running output slot per digit of the chunk
+  uint16_t warp_hist[kWsRankWarps * kRadix];
+  uint32_t bin_start[kRadix];
+  uint32_t bin_count[kRadix];
+  uint32_t gbase[2][kRadix];  // destination of sorted position p = gbase[d] + p
+  uint32_t invdig[2][T];      // sorted position -> (digit << 16) | tile position
+};
+
+template <int T>
+__host__ __device__ constexpr int row_slot(int esz) {
+  return T * esz + 16;
+}
+
+template <int T, int NS>
+__host__ __device__ constexpr size_t ws_header() {
+  return (sizeof(WsShared<T, NS>) + 15) & ~size_t(15);
+}
+
+template <int T, int VB>
+__host__ __device__ constexpr size_t ws_buffer(int order) {
+  return (size_t)order * row_slot<T>(4) + (VB ? row_slot<T>(VB) : 0);
+}
+
+__device__ __forceinline__ uintptr_t row_base(const Cols& c, int r) {
+  return r < c.order ? reinterpret_cast<uintptr_t>(c.in + (int64_t)r * c.in_stride)
+                     : reinterpret_cast<uintptr_t>(c.vin);
+}
+
+template <int T, int NS, int VB>
+__global__ void __launch_bounds__(kWsThreads, 1)
+k_digit_move(Cols c, LargeSegs ls, PassDesc pd, const uint32_t* __restrict__ chunk_off,
+             int* __restrict__ claim, unsigned* status) {
+  constexpr int ITEMS = T / kWsRankThreads;
+  constexpr int WITEMS = T / kWsWriteThreads;
+  extern __shared__ __align__(16) uint8_t smem[];
+  WsShared<T, NS>& S = *reinterpret_cast<WsShared<T, NS>*>(smem);
+  uint8_t* const stage = smem + ws_header<T, NS>();
+  const size_t bufsz = ws_buffer<T, VB>(c.order);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nchunks = n_chunks(ls);
+  const int nrows = c.order + (VB ? 1 : 0);
+  const int nbins = 1 << pd.bits;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&S.full[s], 32);
+      mbar_init(&S.empty[s], kWsWriteThreads);
+    }
+    for (int j = 0; j < 2; ++j) {
+      mbar_init(&S.ranked[j], kWsRankThreads);
+      mbar_init(&S.consumed[j], kWsWriteThreads);
+    }
+  }
+  __syncthreads();
+
+  if (warp == kWsRankWarps + kWsWriteWarps) {
+    // ---------------- producer ----------------
+    int ch = 0, k = 0, ntile = 0;
+    if (lane == 0) ch = atomicAdd(claim, 1);
+    ch = __shfl_sync(0xffffffffu, ch, 0);
+    for (int q = 0;; ++q) {
+      const int s = q % NS;
+      if (q >= NS && !mbar_wait(&S.empty[s], ((q / NS) - 1) & 1, status)) break;
+      TileSlot& ts = S.slot[s];
+      uint8_t* buf = stage + (size_t)s * bufsz;
+      if (ch >= nchunks) {
+        if (lane == 0) ts.chunk = ch;
+        __syncwarp();
+        mbar_arrive(&S.full[s]);
+        break;
+      }
+      const ChunkInfo ci = chunk_info(ls, ch);
+      ntile = (ci.end - ci.start + T - 1) / T;
+      const int start = ci.start + k * T, end = min(start + T, ci.end), n = end - start;
+      // row plans: lane r handles row r
+      unsigned bytes = 0;
+      RowPlan rp;
+      if (lane < nrows) {
+        const int e = lane < c.order ? 4 : VB;
+        const uintptr_t g0 = row_base(c, lane) + (uintptr_t)start * e, g1 = g0 + (uintptr_t)n * e;
+        const uintptr_t a0 = (g0 + 15) & ~uintptr_t(15), a1 = g1 & ~uintptr_t(15);
+        rp.off = (int)(g0 & 15);
+        if (a1 > a0) {
+          rp.head = (int)((a0 - g0) / e);
+          rp.tail_from = (int)((a1 - g0) / e);
+          bytes = (unsigned)(a1 - a0);
+        } else {
+          rp.head = n;
+          rp.tail_from = n;
+        }
+        ts.row[lane] = rp;
+      }
+      if (lane == 0) {
+        ts.chunk = ch;
+        ts.k = k;
+        ts.ntile = ntile;
+        ts.start = start;
+        ts.end = end;
+        ts.lo = ci.lo;
+        ts.hi = ci.hi;
+      }
+      __syncwarp();
+      // unaligned edges with plain loads (the whole warp)
+      for (int r = 0; r < nrows; ++r) {
+        const RowPlan p = ts.row[r];
+        const int nplain = p.head + (n - p.tail_from);
+        uint8_t* dst = buf + (size_t)r * row_slot<T>(4) + p.off;
+        for (int x = lane; x < nplain; x += 32) {
+          const int i = x < p.head ? x : p.tail_from + (x - p.head);
+          if (r < c.order)
+            *reinterpret_cast<uint32_t*>(dst + (size_t)i * 4) =
+                (uint32_t)__ldg(c.in + (int64_t)r * c.in_stride + start + i);
+          else if (VB == 8)
+            *reinterpret_cast<unsigned long long*>(dst + (size_t)i * 8) =
+                __ldg(reinterpret_cast<const unsigned long long*>(c.vin) + start + i);
+          else
+            *reinterpret_cast<uint32_t*>(dst + (size_t)i * 4) =
+                __ldg(reinterpret_cast<const uint32_t*>(c.vin) + start + i);
+        }
+      }
+      // total bytes of the bulk copies, then one transaction-counted arrival
+      unsigned total = bytes;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_expect_tx(&S.full[s], total);
+      else mbar_arrive(&S.full[s]);
+      if (lane < nrows && bytes) {
+        const int e = lane < c.order ? 4 : VB;
+        bulk_g2s(buf + (size_t)lane * row_slot<T>(4) + rp.off + (size_t)rp.head * e,
+                 reinterpret_cast<const void*>(row_base(c, lane) + (uintptr_t)(start + rp.head) * e),
+                 bytes, &S.full[s]);
+      }
+      // next work item
+      if (++k >= ntile) {
+        k = 0;
+        if (lane == 0) ch = atomicAdd(claim, 1);
+        ch = __shfl_sync(0xffffffffu, ch, 0);
+      }
+    }
+  } else if (warp < kWsRankWarps) {
+    // ---------------- rankers ----------------
+    const int w = warp;
+    for (int q = 0;; ++q) {
+      const int s = q % NS, j = q & 1;
+      const bool ok = mbar_wait(&S.full[s], (q / NS) & 1, status);
+      const TileSlot& ts = S.slot[s];
+      const int ch = ts.chunk;
+      if (q >= 2 && !mbar_wait(&S.consumed[j], ((q / 2) - 1) & 1, status)) break;
+      if (ch >= nchunks || !ok) {
+        mbar_arrive(&S.ranked[j]);  // the writers see the end marker too
+        break;
+      }
+      const uint8_t* buf = stage + (size_t)s * bufsz;
+      const int n_valid = ts.end - ts.start;
+      if (ts.k == 0)  // a new chunk: its first output slot per digit
+        for (int d = threadIdx.x; d < nbins; d += kWsRankThreads)
+          S.off[d] = chunk_off[(size_t)ch * kRadix + d];
+      uint32_t dig[ITEMS], rank[ITEMS];
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) dig[i] = 0;
+      for (int f = 0; f < pd.nfields; ++f) {
+        const DigitField fd = pd.f[f];
+        const uint32_t* row = reinterpret_cast<const uint32_t*>(
+            buf + (size_t)fd.mode * row_slot<T>(4) + ts.row[fd.mode].off);
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+          const int pos = w * ITEMS * 32 + i * 32 + lane;
+          if (pos < n_valid) dig[i] |= field_bits(row[pos], fd);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i)
+        if (w * ITEMS * 32 + i * 32 + lane >= n_valid) dig[i] = kRadix - 1;  // padding sorts last
+      block_rank<kWsRankWarps, ITEMS, 1>(dig, rank, S.warp_hist, S.bin_start, S.bin_count);
+      for (int d = threadIdx.x; d < nbins; d += kWsRankThreads) {
+        uint32_t cnt = S.bin_count[d];
+        if (d == kRadix - 1) cnt -= (uint32_t)(T - n_valid);
+        const uint32_t o = S.off[d];
+        S.gbase[j][d] = o - S.bin_start[d];
+        S.off[d] = o + cnt;
+      }
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i)
+        S.invdig[j][rank[i]] = (dig[i] << 16) | (uint32_t)(w * ITEMS * 32 + i * 32 + lane);
+      mbar_arrive(&S.ranked[j]);
+    }
+  } else {
+    // ---------------- writers ----------------
+    const int t = threadIdx.x - kWsRankThreads;
+    for (int q = 0;; ++q) {
+      const int s = q % NS, j = q & 1;
+      if (!mbar_wait(&S.ranked[j], (q / 2) & 1, status)) break;
+      const TileSlot& ts = S.slot[s];
+      if (ts.chunk >= nchunks) break;
+      const uint8_t* buf = stage + (size_t)s * bufsz;
+      const int n_valid = ts.end - ts.start, lo = ts.lo, hi = ts.hi;
+      int dst_pos[WITEMS], src_idx[WITEMS];
+#pragma unroll
+      for (int k = 0; k < WITEMS; ++k) {
+        const int p = k * kWsWriteThreads + t;
+        int g = -1, i = 0;
+        if (p < n_valid) {
+          const uint32_t x = S.invdig[j][p];
+          g = (int)(S.gbase[j][x >> 16] + (uint32_t)p);
+          i = (int)(x & 0xffffu);
+          if (g < lo || g >= hi) g = -1;  // never write outside the bucket
+        }
+        dst_pos[k] = g;
+        src_idx[k] = i;
+      }
+      for (int r = 0; r < c.order; ++r) {
+        const uint32_t* src =
+            reinterpret_cast<const uint32_t*>(buf + (size_t)r * row_slot<T>(4) + ts.row[r].off);
+        int32_t* dst = c.out + (int64_t)r * c.out_stride;
+#pragma unroll
+        for (int k = 0; k < WITEMS; ++k)
+          if (dst_pos[k] >= 0) dst[dst_pos[k]] = (int32_t)src[src_idx[k]];
+      }
+      if constexpr (VB != 0) {
+        using V = typename std::conditional<VB == 8, unsigned long long, uint32_t>::type;
+        const V* src = reinterpret_cast<const V*>(buf + (size_t)c.order * row_slot<T>(4) +
+                                                  ts.row[c.order].off);
+        V* dst = static_cast<V*>(c.vout);
+#pragma unroll
+        for (int k = 0; k < WITEMS; ++k)
+          if (dst_pos[k] >= 0) dst[dst_pos[k]] = src[src_idx[k]];
+      }
+      mbar_arrive(&S.consumed[j]);
+      mbar_arrive(&S.empty[s]);
+    }
+  }
+}
+
+template <int T, int NS, int VB>
+size_t ws_smem(int order) {
+  return ws_header<T, NS>() + NS * ws_buffer<T, VB>(order);
+}
+
+template <int T, int NS, int VB>
+cudaError_t launch_move_t(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
+                          const uint32_t* chunk_off, int* claim, int max_chunks,
+                          unsigned* status, cudaStream_t stream) {
+  const size_t smem = ws_smem<T, NS, VB>(c.order);
+  cudaError_t e = cudaFuncSetAttribute(k_digit_move<T, NS, VB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int grid = sm_count();
+  if (grid > max_chunks) grid = max_chunks;
+  if (grid < 1) grid = 1;
+  k_digit_move<T, NS, VB><<<grid, kWsThreads, smem, stream>>>(c, ls, pd, chunk_off, claim,
+                                                              status);
+  return cudaGetLastError();
+}
+
+// Ring depth for a tile size: three staging buffers when they fit 227 KB of
+// shared memory, else two.
+template <int VB>
+cudaError_t launch_move_vb(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
+                           const uint32_t* chunk_off, int* claim, int max_chunks,
+                           unsigned* status, cudaStream_t stream) {
+  constexpr size_t kMax = 227 * 1024;
+#define QSD_MV(T_, NS_) \
+  return launch_move_t<T_, NS_, VB>(c, ls, pd, chunk_off, claim, max_chunks, status, stream)
+  if (ls.tile == 4096) {
+    if (ws_smem<4096, 3, VB>(c.order) <= kMax) QSD_MV(4096, 3);
+    QSD_MV(4096, 2);
+  }
+  if (ls.tile == 2048) {
+    if (ws_smem<2048, 3, VB>(c.order) <= kMax) QSD_MV(2048, 3);
+    QSD_MV(2048, 2);
+  }
+  if (ws_smem<1024, 3, VB>(c.order) <= kMax) QSD_MV(1024, 3);
+  QSD_MV(1024, 2);
+#undef QSD_MV
+}
+
+}  // namespace
+
+// Entries per tile: the largest of 4096, 2048, 1024 whose two-slot ring fits
+// 227 KB of shared memory (QSD_TILE overrides it for experiments).
+int digit_tile(int order, int vbytes) {
+  if (const char* e = getenv("QSD_TILE")) {
+    const int v = atoi(e);
+    if (v == 1024 || v == 2048 || v == 4096) return v;
+  }
+  auto fits = [&](int T, size_t hdr) {
+    const size_t rows = (size_t)order * (T * 4 + 16) + (vbytes ? (size_t)T * vbytes + 16 : 0);
+    return hdr + 2 * rows <= 227 * 1024;
+  };
+  if (fits(4096, ws_header<4096, 2>())) return 4096;
+  if (fits(2048, ws_header<2048, 2>())) return 2048;
+  return 1024;
+}
+
+// Entries per chunk: 8 tiles (QSD_CHUNK_TILES overrides).
+int digit_chunk(int order, int vbytes) {
+  int k = 8;
+  if (const char* e = getenv("QSD_CHUNK_TILES")) {
+    const int v = atoi(e);
+    if (v >= 1 && v <= 256) k = v;
+  }
+  return k * digit_tile(order, vbytes);
+}
+
+cudaError_t launch_chunk_hist(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
+                              uint32_t* chunk_hist, uint32_t* group_sum, int* claim,
+                              int max_chunks, cudaStream_t stream) {
+  int grid = sm_count() * 8;
+  if (grid > max_chunks) grid = max_chunks;
+  if (grid < 1) grid = 1;
+  k_chunk_hist<<<grid, kHistThreads, 0, stream>>>(c, ls, pd, chunk_hist, group_sum, claim);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_scan(const LargeSegs& ls, uint32_t* chunk_hist,
+                              const uint32_t* group_sum, int max_groups, cudaStream_t stream) {
+  int grid = sm_count() * 8;
+  if (grid > max_groups) grid = max_groups;
+  if (grid < 1) grid = 1;
+  k_chunk_scan<<<grid, kRadix, 0, stream>>>(ls, chunk_hist, group_sum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_digit_move(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
+                              const uint32_t* chunk_off, int* claim, int max_chunks,
+                              unsigned* status, cudaStream_t stream) {
+  switch (c.vbytes) {
+    case 0: return launch_move_vb<0>(c, ls, pd, chunk_off, claim, max_chunks, status, stream);
+    case 4: return launch_move_vb<4>(c, ls, pd, chunk_off, claim, max_chunks, status, stream);
+    case 8: return launch_move_vb<8>(c, ls, pd, chunk_off, claim, max_chunks, status, stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace qsd

@@ -32,9 +32,9 @@ constexpr int64_t kMaxNnz = (int64_t(1) << 30) - 1;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-  size_t status, counters, seg_start, seg_lb, large, tile_base, tile_owner, hist,
-      lb0, lb1, total;
-  int max_large, max_tiles, max_passes;
+  size_t status, counters, seg_start, seg_lb, large, chunk_base, group_base, chunk_owner,
+      group_owner, chunk_hist, group_sum, total;
+  int max_large, max_chunks, max_groups, max_passes;
 };
 
 bool plan_has_prefix_group(const qsd_plan_s* p) {
@@ -43,39 +43,36 @@ bool plan_has_prefix_group(const qsd_plan_s* p) {
   return false;
 }
 
-Layout layout_for(const qsd_plan_s* p, int64_t nnz) {
+Layout layout_for(const qsd_plan_s* p, int64_t nnz, int vbytes) {
   Layout L;
   std::memset(&L, 0, sizeof(L));
-  const int T = onesweep_tile();
+  const int CH = digit_chunk(p->order, vbytes);
   const int C = p->local_capacity;
   int maxp = 0;
   for (int g = 0; g < p->ngroups; ++g) maxp = std::max(maxp, p->groups[g].npasses);
   L.max_passes = std::max(maxp, 1);
   const int64_t n = std::max<int64_t>(nnz, 1);
-  L.max_large = (int)(n / (C + 1) + 1);
-  L.max_tiles = (int)((n + T - 1) / T + L.max_large);
   const bool segs = plan_has_prefix_group(p);
+  L.max_large = segs ? (int)(n / (C + 1) + 1) : 1;
+  L.max_chunks = (int)((n + CH - 1) / CH + L.max_large);
+  L.max_groups = (L.max_chunks + kGroupChunks - 1) / kGroupChunks + L.max_large;
   size_t off = 0;
-  L.status = off;
-  off += align_up(sizeof(unsigned));
-  L.counters = off;
-  off += align_up(sizeof(int) * kNumCounters);
-  L.seg_start = off;
-  off += segs ? align_up(sizeof(int) * (size_t)(n + 2)) : 0;
-  L.seg_lb = off;
-  off += segs ? align_up(sizeof(uint32_t) * (size_t)seg_lookback_words((int)n)) : 0;
-  L.large = off;
-  off += segs ? align_up(sizeof(int2) * (size_t)L.max_large) : 0;
-  L.tile_base = off;
-  off += segs ? align_up(sizeof(int) * (size_t)L.max_large) : 0;
-  L.tile_owner = off;
-  off += segs ? align_up(sizeof(int) * (size_t)L.max_tiles) : 0;
-  L.hist = off;
-  off += align_up(sizeof(uint32_t) * (size_t)L.max_large * L.max_passes * kRadix);
-  L.lb0 = off;
-  off += align_up(sizeof(uint32_t) * (size_t)L.max_tiles * kRadix);
-  L.lb1 = off;
-  off += align_up(sizeof(uint32_t) * (size_t)L.max_tiles * kRadix);
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align_up(bytes);
+    return o;
+  };
+  L.status = take(sizeof(unsigned));
+  L.counters = take(sizeof(int) * kNumCounters);
+  L.seg_start = take(segs ? sizeof(int) * (size_t)(n + 2) : 0);
+  L.seg_lb = take(segs ? sizeof(uint32_t) * (size_t)seg_lookback_words((int)n) : 0);
+  L.large = take(segs ? sizeof(int2) * (size_t)L.max_large : 0);
+  L.chunk_base = take(segs ? sizeof(int) * (size_t)L.max_large : 0);
+  L.group_base = take(segs ? sizeof(int) * (size_t)L.max_large : 0);
+  L.chunk_owner = take(segs ? sizeof(int) * (size_t)L.max_chunks : 0);
+  L.group_owner = take(segs ? sizeof(int) * (size_t)L.max_groups : 0);
+  L.chunk_hist = take(sizeof(uint32_t) * (size_t)L.max_chunks * kRadix);
+  L.group_sum = take(sizeof(uint32_t) * (size_t)L.max_passes * L.max_groups * kRadix);
   L.total = off;
   return L;
 }
@@ -121,11 +118,12 @@ qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
   int* seg_start = reinterpret_cast<int*>(base + L.seg_start);
   uint32_t* seg_lb = reinterpret_cast<uint32_t*>(base + L.seg_lb);
   int2* large = reinterpret_cast<int2*>(base + L.large);
-  int* tile_base = reinterpret_cast<int*>(base + L.tile_base);
-  int* tile_owner = reinterpret_cast<int*>(base + L.tile_owner);
-  uint32_t* hist = reinterpret_cast<uint32_t*>(base + L.hist);
-  uint32_t* lbs[2] = {reinterpret_cast<uint32_t*>(base + L.lb0),
-                      reinterpret_cast<uint32_t*>(base + L.lb1)};
+  int* chunk_base = reinterpret_cast<int*>(base + L.chunk_base);
+  int* group_base = reinterpret_cast<int*>(base + L.group_base);
+  int* chunk_owner = reinterpret_cast<int*>(base + L.chunk_owner);
+  int* group_owner = reinterpret_cast<int*>(base + L.group_owner);
+  uint32_t* chunk_hist = reinterpret_cast<uint32_t*>(base + L.chunk_hist);
+  uint32_t* group_sum = reinterpret_cast<uint32_t*>(base + L.group_sum);
 
   QSD_CUDA(cudaMemsetAsync(base, 0, L.counters + sizeof(int) * kNumCounters, st));
   const bool has_vals = vals && vals->elem_bytes != 0;
@@ -177,7 +175,8 @@ qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
     QSD_LAUNCH(tag("validate", -1, -1, nnz, 4 * plan->order),
                launch_validate(cur.c, cur.stride, plan->order, plan->dims, plan->tau, nnz,
                                status, st));
-  const int T = onesweep_tile();
+  const int T = digit_tile(plan->order, has_vals ? vals->elem_bytes : 0);
+  const int CH = digit_chunk(plan->order, has_vals ? vals->elem_bytes : 0);
   const int C = plan->local_capacity;
 
   for (int gi = 0; gi < plan->ngroups && nnz > 0; ++gi) {
@@ -203,16 +202,19 @@ qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
     LargeSegs ls;
     std::memset(&ls, 0, sizeof(ls));
     ls.nnz = nnz;
+    ls.tile = T;
+    ls.chunk = CH;
     ls.counters = counters;
-    int max_tiles, max_large;
+    int max_chunks, max_groups;
     int64_t large_entries;  // -1: known on the device only
     if (g.prefix_len == 0) {
       ls.single = 1;
-      ls.single_tiles = (nnz + T - 1) / T;
-      max_tiles = ls.single_tiles;
-      max_large = 1;
+      max_chunks = (nnz + CH - 1) / CH;
+      max_groups = (max_chunks + kGroupChunks - 1) / kGroupChunks;
       large_entries = nnz;
-      QSD_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * P * kRadix, st));
+      for (int p = 0; p < P; ++p)
+        QSD_CUDA(cudaMemsetAsync(group_sum + (size_t)p * L.max_groups * kRadix, 0,
+                                 sizeof(uint32_t) * (size_t)max_groups * kRadix, st));
     } else {
       const int32_t* pcols[kMaxOrder];
       for (int i = 0; i < g.prefix_len; ++i)
@@ -222,33 +224,41 @@ qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
                  launch_seg_discover(pcols, g.prefix_len, nnz, seg_start, seg_lb, counters,
                                      status, st));
       QSD_LAUNCH(tag("seg_classify", gi, -1, nnz, 0),
-                 launch_seg_classify(seg_start, counters, nnz, C, T, large, tile_base,
-                                     tile_owner, hist, P, st));
+                 launch_seg_classify(seg_start, counters, nnz, C, CH, large, chunk_base,
+                                     group_base, chunk_owner, group_owner, group_sum, P,
+                                     L.max_groups, st));
       // small buckets: straight into F (in place when F is the input buffer)
       QSD_LAUNCH(tag("local_sort", gi, -1, -1, 2 * R, 1),
                  launch_local_sort(cols(cur, F), pl, seg_start, counters, 0, nnz, C, status,
                                    st));
       ls.single = 0;
       ls.seg = large;
-      ls.tile_base = tile_base;
-      ls.tile_owner = tile_owner;
-      max_tiles = L.max_tiles;
-      max_large = L.max_large;
+      ls.chunk_base = chunk_base;
+      ls.group_base = group_base;
+      ls.chunk_owner = chunk_owner;
+      ls.group_owner = group_owner;
+      max_chunks = L.max_chunks;
+      max_groups = L.max_groups;
       large_entries = -1;
     }
     // Global passes over the large buckets (or the whole tensor).
-    QSD_LAUNCH(tag("digit_hist", gi, -1, large_entries, 4 * g.nkeys),
-               launch_digit_hist(cols(cur, dst(0)), ls, pl, hist, lbs[0], max_tiles, status,
-                                 st));
-    QSD_LAUNCH(tag("digit_scan", gi, -1, large_entries, 0),
-               launch_digit_scan(ls, P, hist, max_large, st));
     for (int p = 0; p < P; ++p) {
       const Src in = p == 0 ? cur : buf_src(dst(p - 1));
-      uint32_t* lb_next = (p + 1 < P) ? lbs[(p + 1) & 1] : nullptr;
-      QSD_LAUNCH(tag("onesweep", gi, p, large_entries, 2 * R),
-                 launch_onesweep_pass(cols(in, dst(p)), ls, g.pass[p], p, P, hist,
-                                      lbs[p & 1], lb_next, counters + kCntPassTile + p,
-                                      max_tiles, status, st));
+      uint32_t* gs = group_sum + (size_t)p * L.max_groups * kRadix;
+      int nf = 0;  // key rows the digit is read from
+      for (int k = 0; k < g.pass[p].nfields; ++k) {
+        bool seen = false;
+        for (int j = 0; j < k; ++j) seen |= g.pass[p].f[j].mode == g.pass[p].f[k].mode;
+        nf += seen ? 0 : 1;
+      }
+      QSD_LAUNCH(tag("chunk_hist", gi, p, large_entries, 4 * nf),
+                 launch_chunk_hist(cols(in, dst(p)), ls, g.pass[p], chunk_hist, gs,
+                                   counters + kCntClaim + 2 * p, max_chunks, st));
+      QSD_LAUNCH(tag("chunk_scan", gi, p, large_entries, 0),
+                 launch_chunk_scan(ls, chunk_hist, gs, max_groups, st));
+      QSD_LAUNCH(tag("digit_move", gi, p, large_entries, 2 * R),
+                 launch_digit_move(cols(in, dst(p)), ls, g.pass[p], chunk_hist,
+                                   counters + kCntClaim + 2 * p + 1, max_chunks, status, st));
     }
     cur = buf_src(F);
   }
@@ -270,7 +280,10 @@ extern "C" {
 qsd_status qsd_workspace_bytes(qsd_plan_t plan, int64_t nnz, size_t* bytes) {
   if (!plan || !bytes || nnz < 0) return QSD_ERR_INVALID_ARGUMENT;
   if (nnz > kMaxNnz) return QSD_ERR_UNSUPPORTED;
-  *bytes = layout_for(plan, nnz).total;
+  // the tile size depends on the value width: take the largest layout
+  size_t b = 0;
+  for (int vb : {0, 4, 8}) b = std::max(b, layout_for(plan, nnz, vb).total);
+  *bytes = b;
   return QSD_OK;
 }
 
@@ -281,7 +294,7 @@ qsd_status qsd_transpose_ws(qsd_coords* coords, qsd_values* vals, int64_t nnz,
   if (s != QSD_OK) return s;
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & (kAlign - 1)))
     return QSD_ERR_INVALID_ARGUMENT;
-  const Layout L = layout_for(plan, nnz);
+  const Layout L = layout_for(plan, nnz, vals ? vals->elem_bytes : 0);
   if (workspace_bytes < L.total) return QSD_ERR_WORKSPACE_TOO_SMALL;
   return run_plan(coords, vals, nullptr, nnz, plan, workspace, L, (cudaStream_t)stream);
 }
@@ -299,7 +312,7 @@ qsd_status qsd_transpose_from_ws(const int32_t* in_coords, int64_t in_stride,
     return QSD_ERR_INVALID_ARGUMENT;
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & (kAlign - 1)))
     return QSD_ERR_INVALID_ARGUMENT;
-  const Layout L = layout_for(plan, nnz);
+  const Layout L = layout_for(plan, nnz, has_vals ? out_vals->elem_bytes : 0);
   if (workspace_bytes < L.total) return QSD_ERR_WORKSPACE_TOO_SMALL;
   Src ext;
   ext.c = in_coords;
@@ -319,7 +332,7 @@ qsd_status qsd_transpose(qsd_coords* coords, qsd_values* vals, int64_t nnz,
   qsd_status s = check_buffers(coords, vals, nnz, plan);
   if (s != QSD_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
-  const Layout L = layout_for(plan, nnz);
+  const Layout L = layout_for(plan, nnz, vals ? vals->elem_bytes : 0);
   void* ws = nullptr;
   if (cudaMallocAsync(&ws, L.total, st) != cudaSuccess) {
     cudaGetLastError();

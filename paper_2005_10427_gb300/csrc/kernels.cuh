@@ -10,14 +10,18 @@ namespace qsd {
 
 // Workspace counter slots (int32), zeroed before every group.
 enum Counter {
-  kCntSegTile = 0,   // dynamic tile id of the bucket discovery kernel
-  kCntNumSeg = 1,    // number of buckets found
-  kCntNumLarge = 2,  // number of buckets too large for one thread block
-  kCntNumTiles = 3,  // digit-pass tiles over all large buckets
-  kCntLargeEntries = 4,  // entries inside large buckets
-  kCntPassTile = 5,  // dynamic tile ids of the digit passes: 5 .. 5+kMaxPasses
-  kNumCounters = 5 + kMaxPasses
+  kCntSegTile = 0,       // dynamic tile id of the bucket discovery kernel
+  kCntNumSeg = 1,        // number of buckets found
+  kCntNumLarge = 2,      // buckets too large for one thread block
+  kCntNumChunks = 3,     // chunks over all large buckets
+  kCntNumGroups = 4,     // chunk groups over all large buckets
+  kCntLargeEntries = 5,  // entries inside large buckets
+  kCntClaim = 6,         // per pass: chunk claims of the histogram and move kernels
+  kNumCounters = 6 + 2 * kMaxPasses
 };
+
+// Chunks per chunk group (the unit of the offset scan).
+constexpr int kGroupChunks = 64;
 
 // Structure-of-arrays tensor buffers as the kernels see them.
 struct Cols {
@@ -31,16 +35,21 @@ struct Cols {
   int vbytes;          // 0, 4 or 8
 };
 
-// The buckets handled by the global digit passes. When `single` is set there
-// is one bucket [0, nnz) and no device tables.
+// The buckets sorted by the global digit passes, cut into chunks (contiguous
+// entry ranges of at most `chunk` entries inside one bucket) and chunk
+// groups (kGroupChunks consecutive chunks of one bucket). When `single` is
+// set there is one bucket [0, nnz) and the tables are implicit.
 struct LargeSegs {
   int single;
   int nnz;
-  int single_tiles;          // tiles of the single bucket
-  const int* counters;       // kCntNumLarge / kCntNumTiles
-  const int2* seg;           // [start, end) of each large bucket
-  const int* tile_base;      // first tile of each large bucket
-  const int* tile_owner;     // large bucket of each tile
+  int tile;                 // entries per tile (the unit staged in shared memory)
+  int chunk;                // entries per chunk, a multiple of tile
+  const int* counters;      // kCntNumLarge / kCntNumChunks / kCntNumGroups
+  const int2* seg;          // [start, end) of each large bucket
+  const int* chunk_base;    // first chunk of each large bucket
+  const int* group_base;    // first group of each large bucket
+  const int* chunk_owner;   // large bucket of each chunk
+  const int* group_owner;   // large bucket of each group
 };
 
 struct PassList {
@@ -53,27 +62,33 @@ cudaError_t launch_seg_discover(const int32_t* const* prefix_cols, int nprefix,
                                 int nnz, int* seg_start, uint32_t* seg_lb,
                                 int* counters, unsigned* status,
                                 cudaStream_t stream);
-cudaError_t launch_seg_classify(const int* seg_start, int* counters, int nnz,
-                                int small_max, int tile, int2* large,
-                                int* tile_base, int* tile_owner, uint32_t* hist,
-                                int npasses, cudaStream_t stream);
+// Buckets larger than small_max are numbered and cut into chunks of `chunk`
+// entries and groups of kGroupChunks chunks; their group sums for every pass
+// (group_sum[pass][group][kRadix]) are zeroed.
+cudaError_t launch_seg_classify(const int* seg_start, int* counters, int nnz, int small_max,
+                                int chunk, int2* large, int* chunk_base, int* group_base,
+                                int* chunk_owner, int* group_owner, uint32_t* group_sum,
+                                int npasses, int max_groups, cudaStream_t stream);
 cudaError_t launch_validate(const int32_t* coords, int64_t stride, int order,
                             const int64_t* dims, const int* tau, int nnz,
                             unsigned* status, cudaStream_t stream);
 
-int onesweep_tile();  // entries per digit-pass tile
-cudaError_t launch_digit_hist(const Cols& c, const LargeSegs& ls,
-                              const PassList& pl, uint32_t* hist, uint32_t* lb0,
-                              int max_tiles, unsigned* status,
-                              cudaStream_t stream);
-cudaError_t launch_digit_scan(const LargeSegs& ls, int npasses, uint32_t* hist,
-                              int max_large, cudaStream_t stream);
-cudaError_t launch_onesweep_pass(const Cols& c, const LargeSegs& ls,
-                                 const PassDesc& pd, int pass_index, int npasses,
-                                 const uint32_t* digit_base, uint32_t* lb,
-                                 uint32_t* lb_next, int* tile_counter,
-                                 int max_tiles, unsigned* status,
-                                 cudaStream_t stream);
+// Global digit passes (reduce, scan, move):
+int digit_tile(int order, int vbytes);   // entries per tile
+int digit_chunk(int order, int vbytes);  // entries per chunk
+// Per chunk: histogram of the pass's digit into chunk_hist[chunk][kRadix];
+// adds each chunk's counts into group_sum[group][kRadix] (zeroed before).
+cudaError_t launch_chunk_hist(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
+                              uint32_t* chunk_hist, uint32_t* group_sum, int* claim,
+                              int max_chunks, cudaStream_t stream);
+// Per chunk group: turns chunk_hist into each chunk's first output slot per
+// digit (bucket start + digits below + the same digit in earlier chunks).
+cudaError_t launch_chunk_scan(const LargeSegs& ls, uint32_t* chunk_hist,
+                              const uint32_t* group_sum, int max_groups, cudaStream_t stream);
+// Moves every row of every chunk to its digit's slots, tile by tile.
+cudaError_t launch_digit_move(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
+                              const uint32_t* chunk_off, int* claim, int max_chunks,
+                              unsigned* status, cudaStream_t stream);
 
 cudaError_t launch_local_sort(const Cols& c, const PassList& pl,
                               const int* seg_start, const int* counters,

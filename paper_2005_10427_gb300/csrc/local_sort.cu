@@ -35,7 +35,7 @@ struct LsVal<8> {
 
 template <int CAP>
 struct LsShared {
-  uint32_t warp_hist[kLsWarps * kRadix];
+  uint16_t warp_hist[kLsWarps * kRadix];
   uint32_t bin_start[kRadix];
   uint32_t bin_count[kRadix];
   uint32_t tmp[kLsWarps + 1];

@@ -92,28 +92,34 @@ k_seg_discover(PrefixCols pc, int nnz, int ntiles, int* __restrict__ seg_start,
 }
 
 // Buckets larger than small_max go to the digit passes: each gets an index,
-// a contiguous range of tile ids (so look-back inside a bucket walks t-1,
-// t-2, ...) and a zeroed histogram row for every pass.
-__global__ void k_seg_classify(const int* __restrict__ seg_start,
-                               int* __restrict__ counters, int small_max,
-                               int tile, int2* __restrict__ large,
-                               int* __restrict__ tile_base,
-                               int* __restrict__ tile_owner,
-                               uint32_t* __restrict__ hist, int npasses) {
+// a contiguous range of chunk ids and of chunk-group ids (so a bucket's
+// chunks are consecutive), and zeroed group sums for every pass.
+__global__ void k_seg_classify(const int* __restrict__ seg_start, int* __restrict__ counters,
+                               int small_max, int chunk, int2* __restrict__ large,
+                               int* __restrict__ chunk_base, int* __restrict__ group_base,
+                               int* __restrict__ chunk_owner, int* __restrict__ group_owner,
+                               uint32_t* __restrict__ group_sum, int npasses, int max_groups) {
   const int nseg = counters[kCntNumSeg];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nseg;
-       i += gridDim.x * blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nseg; i += gridDim.x * blockDim.x) {
     const int a = seg_start[i], b = seg_start[i + 1];
     if (b - a <= small_max) continue;
     const int idx = atomicAdd(&counters[kCntNumLarge], 1);
-    const int nt = (b - a + tile - 1) / tile;
-    const int tb = atomicAdd(&counters[kCntNumTiles], nt);
+    const int nc = (b - a + chunk - 1) / chunk;
+    const int ng = (nc + kGroupChunks - 1) / kGroupChunks;
+    const int cb = atomicAdd(&counters[kCntNumChunks], nc);
+    const int gb = atomicAdd(&counters[kCntNumGroups], ng);
     atomicAdd(&counters[kCntLargeEntries], b - a);
     large[idx] = make_int2(a, b);
-    tile_base[idx] = tb;
-    for (int j = 0; j < nt; ++j) tile_owner[tb + j] = idx;
-    uint32_t* hrow = hist + (size_t)idx * npasses * kRadix;
-    for (int j = 0; j < npasses * kRadix; ++j) hrow[j] = 0;
+    chunk_base[idx] = cb;
+    group_base[idx] = gb;
+    for (int j = 0; j < nc; ++j) chunk_owner[cb + j] = idx;
+    for (int j = 0; j < ng; ++j) {
+      group_owner[gb + j] = idx;
+      for (int p = 0; p < npasses; ++p) {
+        uint4* row = reinterpret_cast<uint4*>(group_sum + ((size_t)p * max_groups + gb + j) * kRadix);
+        for (int k = 0; k < kRadix / 4; ++k) row[k] = make_uint4(0, 0, 0, 0);
+      }
+    }
   }
 }
 
@@ -170,19 +176,19 @@ cudaError_t launch_seg_discover(const int32_t* const* prefix_cols, int nprefix,
 
 int seg_lookback_words(int nnz) { return (nnz + kSegTile - 1) / kSegTile + 1; }
 
-cudaError_t launch_seg_classify(const int* seg_start, int* counters, int nnz,
-                                int small_max, int tile, int2* large,
-                                int* tile_base, int* tile_owner, uint32_t* hist,
-                                int npasses, cudaStream_t stream) {
+cudaError_t launch_seg_classify(const int* seg_start, int* counters, int nnz, int small_max,
+                                int chunk, int2* large, int* chunk_base, int* group_base,
+                                int* chunk_owner, int* group_owner, uint32_t* group_sum,
+                                int npasses, int max_groups, cudaStream_t stream) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int blocks = (nnz + 255) / 256;
   if (blocks > sms * 8) blocks = sms * 8;
   if (blocks < 1) blocks = 1;
-  k_seg_classify<<<blocks, 256, 0, stream>>>(seg_start, counters, small_max, tile,
-                                             large, tile_base, tile_owner, hist,
-                                             npasses);
+  k_seg_classify<<<blocks, 256, 0, stream>>>(seg_start, counters, small_max, chunk, large,
+                                             chunk_base, group_base, chunk_owner, group_owner,
+                                             group_sum, npasses, max_groups);
   return cudaGetLastError();
 }
 
