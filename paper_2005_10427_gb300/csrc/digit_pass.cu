@@ -220,11 +220,13 @@ k_chunk_scan(LargeSegs ls, uint32_t* __restrict__ chunk_hist,
 // Hand-offs use mbarriers (every wait bounded); the rankers synchronise
 // among themselves on named barrier 1.
 
-constexpr int kWsRankWarps = 8;
-constexpr int kWsWriteWarps = 8;
-constexpr int kWsRankThreads = kWsRankWarps * 32;
-constexpr int kWsWriteThreads = kWsWriteWarps * 32;
-constexpr int kWsThreads = kWsRankThreads + kWsWriteThreads + 32;  // + producer warp
+// Role sizes: RW ranking warps, WW writing warps, one producer warp.
+template <int RW, int WW>
+struct Roles {
+  static constexpr int kRank = RW * 32;
+  static constexpr int kWrite = WW * 32;
+  static constexpr int kThreads = kRank + kWrite + 32;
+};
 
 // Where one row of a tile lands in its shared-memory slot: entry i is at
 // byte off + i * esz; entries [0, head) and [tail_from, n) arrive by plain
@@ -241,7 +243,7 @@ struct TileSlot {
   RowPlan row[kMaxRows];
 };
 
-template <int T, int NS>
+template <int T, int NS, int RW>
 struct WsShared {
   uint64_t full[NS];     // producer -> rankers: tile staged
   uint64_t empty[NS];    // writers -> producer: staging buffer free
@@ -249,7 +251,7 @@ struct WsShared {
   uint64_t consumed[2];  // writers -> rankers: destinations used
   TileSlot slot[NS];
   uint32_t off[kRadix];  // rankers: running output slot per digit of the chunk
-  uint16_t warp_hist[kWsRankWarps * kRadix];
+  uint16_t warp_hist[RW * kRadix];
   uint32_t bin_start[kRadix];
   uint32_t bin_count[kRadix];
   uint32_t gbase[2][kRadix];  // destination of sorted position p = gbase[d] + p
@@ -261,9 +263,9 @@ __host__ __device__ constexpr int row_slot(int esz) {
   return T * esz + 16;
 }
 
-template <int T, int NS>
+template <int T, int NS, int RW>
 __host__ __device__ constexpr size_t ws_header() {
-  return (sizeof(WsShared<T, NS>) + 15) & ~size_t(15);
+  return (sizeof(WsShared<T, NS, RW>) + 15) & ~size_t(15);
 }
 
 template <int T, int VB>
@@ -276,15 +278,19 @@ __device__ __forceinline__ uintptr_t row_base(const Cols& c, int r) {
                      : reinterpret_cast<uintptr_t>(c.vin);
 }
 
-template <int T, int NS, int VB>
-__global__ void __launch_bounds__(kWsThreads, 1)
+template <int T, int NS, int VB, int RW, int WW>
+__global__ void __launch_bounds__(Roles<RW, WW>::kThreads, 1)
 k_digit_move(Cols c, LargeSegs ls, PassDesc pd, const uint32_t* __restrict__ chunk_off,
              int* __restrict__ claim, unsigned* status) {
+  constexpr int kWsRankWarps = RW, kWsWriteWarps = WW;
+  constexpr int kWsRankThreads = Roles<RW, WW>::kRank;
+  constexpr int kWsWriteThreads = Roles<RW, WW>::kWrite;
   constexpr int ITEMS = T / kWsRankThreads;
-  constexpr int WITEMS = T / kWsWriteThreads;
+  static_assert(ITEMS * kWsRankThreads == T, "rankers must cover the tile");
+  constexpr int WITEMS = (T + kWsWriteThreads - 1) / kWsWriteThreads;
   extern __shared__ __align__(16) uint8_t smem[];
-  WsShared<T, NS>& S = *reinterpret_cast<WsShared<T, NS>*>(smem);
-  uint8_t* const stage = smem + ws_header<T, NS>();
+  WsShared<T, NS, RW>& S = *reinterpret_cast<WsShared<T, NS, RW>*>(smem);
+  uint8_t* const stage = smem + ws_header<T, NS, RW>();
   const size_t bufsz = ws_buffer<T, VB>(c.order);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nchunks = n_chunks(ls);
@@ -423,7 +429,7 @@ k_digit_move(Cols c, LargeSegs ls, PassDesc pd, const uint32_t* __restrict__ chu
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i)
         if (w * ITEMS * 32 + i * 32 + lane >= n_valid) dig[i] = kRadix - 1;  // padding sorts last
-      block_rank<kWsRankWarps, ITEMS, 1>(dig, rank, S.warp_hist, S.bin_start, S.bin_count);
+      block_rank<RW, ITEMS, 1>(dig, rank, S.warp_hist, S.bin_start, S.bin_count);
       for (int d = threadIdx.x; d < nbins; d += kWsRankThreads) {
         uint32_t cnt = S.bin_count[d];
         if (d == kRadix - 1) cnt -= (uint32_t)(T - n_valid);
@@ -483,25 +489,40 @@ k_digit_move(Cols c, LargeSegs ls, PassDesc pd, const uint32_t* __restrict__ chu
   }
 }
 
-template <int T, int NS, int VB>
+template <int T, int NS, int VB, int RW>
 size_t ws_smem(int order) {
-  return ws_header<T, NS>() + NS * ws_buffer<T, VB>(order);
+  return ws_header<T, NS, RW>() + NS * ws_buffer<T, VB>(order);
 }
 
-template <int T, int NS, int VB>
+template <int T, int NS, int VB, int RW, int WW>
 cudaError_t launch_move_t(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
                           const uint32_t* chunk_off, int* claim, int max_chunks,
                           unsigned* status, cudaStream_t stream) {
-  const size_t smem = ws_smem<T, NS, VB>(c.order);
-  cudaError_t e = cudaFuncSetAttribute(k_digit_move<T, NS, VB>,
+  const size_t smem = ws_smem<T, NS, VB, RW>(c.order);
+  cudaError_t e = cudaFuncSetAttribute(k_digit_move<T, NS, VB, RW, WW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = sm_count();
   if (grid > max_chunks) grid = max_chunks;
   if (grid < 1) grid = 1;
-  k_digit_move<T, NS, VB><<<grid, kWsThreads, smem, stream>>>(c, ls, pd, chunk_off, claim,
-                                                              status);
+  k_digit_move<T, NS, VB, RW, WW><<<grid, Roles<RW, WW>::kThreads, smem, stream>>>(
+      c, ls, pd, chunk_off, claim, status);
   return cudaGetLastError();
+}
+
+// Staging slots wanted for 2048-entry tiles (QSD_NS=3..5; default 3).
+int ws_slots() {
+  if (const char* e = getenv("QSD_NS")) {
+    const int v = atoi(e);
+    return v < 3 ? 3 : (v > 5 ? 5 : v);
+  }
+  return 3;
+}
+
+// Warps per role (QSD_WS=8 for 8+8, 16 for 16+15; default 16).
+int ws_width() {
+  if (const char* e = getenv("QSD_WS")) return atoi(e) == 8 ? 8 : 16;
+  return 16;
 }
 
 // Ring depth for a tile size: three staging buffers when they fit 227 KB of
@@ -511,18 +532,31 @@ cudaError_t launch_move_vb(const Cols& c, const LargeSegs& ls, const PassDesc& p
                            const uint32_t* chunk_off, int* claim, int max_chunks,
                            unsigned* status, cudaStream_t stream) {
   constexpr size_t kMax = 227 * 1024;
-#define QSD_MV(T_, NS_) \
-  return launch_move_t<T_, NS_, VB>(c, ls, pd, chunk_off, claim, max_chunks, status, stream)
+#define QSD_MV(T_, NS_, RW_, WW_)                                                      \
+  return launch_move_t<T_, NS_, VB, RW_, WW_>(c, ls, pd, chunk_off, claim, max_chunks, status, \
+                                              stream)
+  const bool wide = ws_width() == 16;
   if (ls.tile == 4096) {
-    if (ws_smem<4096, 3, VB>(c.order) <= kMax) QSD_MV(4096, 3);
-    QSD_MV(4096, 2);
+    if (wide) {
+      if (ws_smem<4096, 3, VB, 16>(c.order) <= kMax) QSD_MV(4096, 3, 16, 15);
+      QSD_MV(4096, 2, 16, 15);
+    }
+    if (ws_smem<4096, 3, VB, 8>(c.order) <= kMax) QSD_MV(4096, 3, 8, 8);
+    QSD_MV(4096, 2, 8, 8);
   }
   if (ls.tile == 2048) {
-    if (ws_smem<2048, 3, VB>(c.order) <= kMax) QSD_MV(2048, 3);
-    QSD_MV(2048, 2);
+    if (wide) {
+      const int ns = ws_slots();
+      if (ns >= 5 && ws_smem<2048, 5, VB, 16>(c.order) <= kMax) QSD_MV(2048, 5, 16, 15);
+      if (ns >= 4 && ws_smem<2048, 4, VB, 16>(c.order) <= kMax) QSD_MV(2048, 4, 16, 15);
+      if (ws_smem<2048, 3, VB, 16>(c.order) <= kMax) QSD_MV(2048, 3, 16, 15);
+      QSD_MV(2048, 2, 16, 15);
+    }
+    if (ws_smem<2048, 3, VB, 8>(c.order) <= kMax) QSD_MV(2048, 3, 8, 8);
+    QSD_MV(2048, 2, 8, 8);
   }
-  if (ws_smem<1024, 3, VB>(c.order) <= kMax) QSD_MV(1024, 3);
-  QSD_MV(1024, 2);
+  if (ws_smem<1024, 3, VB, 8>(c.order) <= kMax) QSD_MV(1024, 3, 8, 8);
+  QSD_MV(1024, 2, 8, 8);
 #undef QSD_MV
 }
 
@@ -539,8 +573,8 @@ int digit_tile(int order, int vbytes) {
     const size_t rows = (size_t)order * (T * 4 + 16) + (vbytes ? (size_t)T * vbytes + 16 : 0);
     return hdr + 2 * rows <= 227 * 1024;
   };
-  if (fits(4096, ws_header<4096, 2>())) return 4096;
-  if (fits(2048, ws_header<2048, 2>())) return 2048;
+  if (fits(4096, ws_header<4096, 2, 16>())) return 4096;
+  if (fits(2048, ws_header<2048, 2, 16>())) return 2048;
   return 1024;
 }
 
