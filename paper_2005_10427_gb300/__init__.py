@@ -31,7 +31,7 @@ class QsdError(RuntimeError):
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _build
+    from .buildlib import build as _build
     return _build(force=force)
 
 
