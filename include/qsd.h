@@ -179,6 +179,29 @@ qsd_status qsd_transpose_from_ws(const int32_t* in_coords, int64_t in_stride,
                                  qsd_plan_t plan, void* workspace,
                                  size_t workspace_bytes, void* stream);
 
+/* Transposes exactly like qsd_transpose_ws, but allocates nothing and takes
+ * no workspace: for callers that cannot allocate device memory, such as code
+ * that runs inside a host framework or serving engine which owns all device
+ * memory through its own allocator and budget, or a latency-critical path
+ * where a device allocation (which can synchronise the device) is not
+ * acceptable. (The paper has no counterpart; this is a library service.)
+ *
+ * Scratch comes from one file-scope device array of 64 MiB that every GPU
+ * loading this library reserves until the process exits. Requests whose
+ * qsd_workspace_bytes(plan, nnz) exceeds 64 MiB are rejected with
+ * QSD_ERR_WORKSPACE_TOO_SMALL before anything is enqueued (for plans with a
+ * bucketed group that is roughly 12 million entries; use qsd_transpose_ws
+ * beyond that). All calls on a device share the array and each call resets
+ * the parts that must start at zero, so calls that may overlap on the GPU
+ * (different streams, or streams not ordered with each other) race and must
+ * not be issued; calls ordered on one stream are fine. The first call on each
+ * device resolves the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture. The launch profiler
+ * (qsd_profile_enable) must be off, as it allocates its own buffers.
+ * Arguments, result buffers and errors are as for qsd_transpose_ws. */
+qsd_status qsd_transpose_noalloc(qsd_coords* coords, qsd_values* vals,
+                                 int64_t nnz, qsd_plan_t plan, void* stream);
+
 /* End-to-end transpose of HOST arrays: copies the input (host_coords rows of
  * length nnz at host_stride, host_vals) into the caller's device double
  * buffers, transposes with `workspace`, copies the result into host_out_*,

@@ -17,7 +17,7 @@ from typing import List, Optional, Sequence, Tuple
 from . import _capi
 
 __all__ = ["Plan", "QsdError", "transpose", "transpose_buffers", "transpose_from",
-           "transpose_host",
+           "transpose_host", "transpose_noalloc",
            "get_async_status", "workspace_status", "build", "lib", "LIB_PATH"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libqsd.so")
@@ -173,6 +173,29 @@ def transpose_from(in_coords, in_vals, cbuf: Sequence, vbuf: Optional[Sequence],
         ctypes.c_void_p(workspace.data_ptr()), int(workspace.numel()),
         _stream_handle(stream))
     _check(st, "qsd_transpose_from_ws")
+    return int(c.selector)
+
+
+def transpose_noalloc(cbuf: Sequence, vbuf: Optional[Sequence], selector: int, nnz: int,
+                      plan: Plan, stream=None) -> int:
+    """qsd_transpose_noalloc on explicit double buffers: like transpose_buffers
+    but with the library's fixed 64 MiB device scratch instead of a workspace,
+    for callers that cannot allocate device memory. Returns the result's
+    selector."""
+    c = _capi.Coords()
+    c.buf[0] = cbuf[0].data_ptr()
+    c.buf[1] = cbuf[1].data_ptr()
+    c.stride = int(cbuf[0].stride(0)) if cbuf[0].dim() == 2 else int(nnz)
+    c.selector = int(selector)
+    v = _capi.Values()
+    if vbuf is not None:
+        v.buf[0] = vbuf[0].data_ptr()
+        v.buf[1] = vbuf[1].data_ptr()
+        v.elem_bytes = _val_bytes(vbuf[0])
+        v.selector = int(selector)
+    st = lib().qsd_transpose_noalloc(ctypes.byref(c), ctypes.byref(v), int(nnz), plan.handle,
+                                     _stream_handle(stream))
+    _check(st, "qsd_transpose_noalloc")
     return int(c.selector)
 
 

@@ -62,6 +62,7 @@ SIGNATURES = [
                              ctypes.c_size_t, P]),
     ("qsd_transpose_from_ws", I, [P, I64, P, ctypes.POINTER(Coords), ctypes.POINTER(Values),
                                   I64, P, P, ctypes.c_size_t, P]),
+    ("qsd_transpose_noalloc", I, [ctypes.POINTER(Coords), ctypes.POINTER(Values), I64, P, P]),
     ("qsd_transpose_host", I, [P, I64, P, P, I64, P, I64, P, ctypes.POINTER(Coords),
                                ctypes.POINTER(Values), P, ctypes.c_size_t, P]),
     ("qsd_workspace_status", I, [P, P, ctypes.POINTER(I)]),

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "kernels.cuh"
 
@@ -383,6 +384,51 @@ qsd_status qsd_transpose_host(const int32_t* host_coords, int64_t host_stride,
   s = qsd_workspace_status(workspace, stream, &dev_status);
   if (s != QSD_OK) return s;
   return dev_status;
+}
+
+// ---------------------------------------------------------------------------
+// Transposition that allocates nothing. Its scratch is this file-scope device
+// array, reserved when the library is loaded onto a GPU and held until the
+// process exits; every call on a device shares it.
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;  // 64 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (the host-side
+// symbol is only a stand-in). Resolved once per device.
+qsd_status noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return QSD_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return QSD_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return QSD_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return QSD_OK;
+}
+}  // namespace
+
+qsd_status qsd_transpose_noalloc(qsd_coords* coords, qsd_values* vals, int64_t nnz,
+                                 qsd_plan_t plan, void* stream) {
+  qsd_status s = check_buffers(coords, vals, nnz, plan);
+  if (s != QSD_OK) return s;
+  const Layout L = layout_for(plan, nnz, vals ? vals->elem_bytes : 0);
+  if (L.total > kNoAllocScratchBytes) return QSD_ERR_WORKSPACE_TOO_SMALL;
+  void* ws = nullptr;
+  s = noalloc_scratch(&ws);
+  if (s != QSD_OK) return s;
+  // run_plan clears the status word and counters it relies on before use
+  return run_plan(coords, vals, nullptr, nnz, plan, ws, L, (cudaStream_t)stream);
 }
 
 qsd_status qsd_workspace_status(const void* workspace, void* stream, qsd_status* out) {
