@@ -52,7 +52,7 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -68,7 +68,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -129,7 +129,7 @@ def committed_traffic(kernel: str, workload: str):
     return d.get(workload, {}).get(kernel)
 
 
-def cpu_oracle_rate(t_coords: np.ndarray, t_vals: np.ndarray, perms, target_s=12.0):
+def cpu_oracle_rate(t_coords: np.ndarray, t_vals: np.ndarray, perms, target_s=15.0):
     """The oracle (single-threaded std::stable_sort) on a prefix sample."""
     import oracle
     n_total = t_coords.shape[1]
@@ -138,8 +138,8 @@ def cpu_oracle_rate(t_coords: np.ndarray, t_vals: np.ndarray, perms, target_s=12
     for sigma in perms:
         oracle.transpose(t_coords[:, :m], t_vals[:m], sigma)
     dt = time.perf_counter() - t0
-    # grow the sample towards target_s seconds of work
-    scale = max(1.0, target_s / max(dt, 1e-3))
+    # grow the sample towards target_s seconds of work (n log n: aim a bit low)
+    scale = max(1.0, 0.7 * target_s / max(dt, 1e-3))
     m2 = int(min(n_total, m * scale))
     if m2 > m:
         m = m2
@@ -191,7 +191,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="qsd", choices=["qsd", "reference"])
     ap.add_argument("--workload", default="nell2like", choices=sorted(WORKLOADS))

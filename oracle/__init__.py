@@ -83,3 +83,24 @@ def permutation(coords: np.ndarray, sigma) -> np.ndarray:
     if rc != 0:
         raise ValueError("oracle rejected its arguments")
     return perm
+
+
+def rank_under(coords: np.ndarray, sigma, entry) -> tuple:
+    """(#entries strictly less than `entry`, #entries equal to it) under the
+    sigma-lexicographic order of Section 2, counted directly over all entries.
+
+    For a transposition this fixes where `entry` lands: a stable sort places
+    the entries equal to it at positions [less, less + equal). Plain numpy,
+    O(r * nnz) per call; used to check single output positions of tensors too
+    large for the full oracle.
+    """
+    coords = np.asarray(coords)
+    nnz = coords.shape[1]
+    lt = np.zeros(nnz, dtype=bool)
+    eq = np.ones(nnz, dtype=bool)
+    for m in sigma:
+        col = coords[m]
+        v = entry[m]
+        lt |= eq & (col < v)
+        eq &= col == v
+    return int(lt.sum()), int(eq.sum())

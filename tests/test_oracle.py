@@ -148,3 +148,19 @@ def test_rejects_bad_permutation():
         oracle.transpose(c, None, [0, 0, 1])
     with pytest.raises(ValueError):
         oracle.transpose(c, None, [0, 1, 3])
+
+
+def test_rank_under_matches_the_stable_sort():
+    rng = np.random.default_rng(17)
+    for r in (2, 3, 4):
+        dims = [int(x) for x in rng.integers(2, 9, size=r)]
+        coords = np.stack([rng.integers(0, d, size=2000) for d in dims]).astype(np.int32)
+        sigma = [int(x) for x in rng.permutation(r)]
+        perm = oracle.permutation(coords, sigma)
+        out = coords[:, perm]
+        for p in rng.choice(coords.shape[1], 40, replace=False):
+            less, equal = oracle.rank_under(coords, sigma, out[:, p])
+            assert less <= p < less + equal
+        # the first entry of each run of equal coordinates sits exactly at `less`
+        less, equal = oracle.rank_under(coords, sigma, out[:, 0])
+        assert less == 0 and equal >= 1
