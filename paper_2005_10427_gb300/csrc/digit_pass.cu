@@ -35,7 +35,6 @@ namespace {
 
 constexpr int kHistThreads = 256;
 constexpr int kHistWarps = kHistThreads / 32;
-constexpr int kHistRun = 8;  // consecutive entries per thread
 constexpr int kMaxRows = kMaxOrder + 1;
 
 int sm_count() {
@@ -89,8 +88,9 @@ __device__ __forceinline__ ChunkInfo chunk_info(const LargeSegs& ls, int c) {
 }
 
 // ---------------------------------------------------------------------------
-// Chunk histograms. Each thread counts kHistRun consecutive entries into its
-// warp's histogram, one shared atomic per run of equal digits.
+// Chunk histograms: 16-byte loads of the digit's rows (four in flight per
+// thread), each vector of four consecutive entries counted into the warp's
+// histogram with one shared atomic per run of equal digits.
 __global__ void __launch_bounds__(kHistThreads)
 k_chunk_hist(Cols c, LargeSegs ls, PassDesc pd, uint32_t* __restrict__ chunk_hist,
              uint32_t* __restrict__ group_sum, int* __restrict__ claim) {
@@ -99,6 +99,10 @@ k_chunk_hist(Cols c, LargeSegs ls, PassDesc pd, uint32_t* __restrict__ chunk_his
   const int w = threadIdx.x >> 5;
   const int nc = n_chunks(ls);
   const int nbins = 1 << pd.bits;
+  // vectors line up across the digit's rows when there is one row, or when the
+  // rows are 16-byte aligned and the stride is a multiple of 4 entries
+  const bool vec = pd.nfields == 1 || ((c.in_stride & 3) == 0 &&
+                                       (reinterpret_cast<uintptr_t>(c.in) & 15) == 0);
   while (true) {
     for (int i = threadIdx.x; i < kHistWarps * kRadix; i += kHistThreads)
       (&s_hist[0][0])[i] = 0;
@@ -107,35 +111,67 @@ k_chunk_hist(Cols c, LargeSegs ls, PassDesc pd, uint32_t* __restrict__ chunk_his
     const int ch = s_chunk;
     if (ch >= nc) break;
     const ChunkInfo ci = chunk_info(ls, ch);
-    for (int base = ci.start + threadIdx.x * kHistRun; base < ci.end;
-         base += kHistThreads * kHistRun) {
-      const int n = min(kHistRun, ci.end - base);
-      uint32_t d[kHistRun];
-#pragma unroll
-      for (int k = 0; k < kHistRun; ++k) d[k] = 0;
+    // Vector path: the digit's rows advance together in 16-byte steps when the
+    // row stride is a multiple of 4 entries; entries before the first aligned
+    // one and after the last full vector are counted one by one.
+    int vbeg = ci.end, vend = ci.end;
+    if (vec) {
+      const uintptr_t a0 = reinterpret_cast<uintptr_t>(c.in + (int64_t)pd.f[0].mode * c.in_stride +
+                                                       ci.start);
+      const int skip = (int)(((16 - (a0 & 15)) & 15) >> 2);
+      vbeg = min(ci.start + skip, ci.end);
+      vend = vbeg + ((ci.end - vbeg) & ~3);
+    }
+    const int nhead = vbeg - ci.start, ntail = ci.end - vend;
+    for (int k = threadIdx.x; k < nhead + ntail; k += kHistThreads) {
+      const int j = k < nhead ? ci.start + k : vend + (k - nhead);
+      uint32_t d = 0;
       for (int f = 0; f < pd.nfields; ++f) {
         const DigitField fd = pd.f[f];
-        const int32_t* col = c.in + (int64_t)fd.mode * c.in_stride + base;
-        uint32_t v[kHistRun];
-#pragma unroll
-        for (int k = 0; k < kHistRun; ++k) v[k] = k < n ? (uint32_t)__ldg(col + k) : 0u;
-#pragma unroll
-        for (int k = 0; k < kHistRun; ++k) d[k] |= field_bits(v[k], fd);
+        d |= field_bits((uint32_t)__ldg(c.in + (int64_t)fd.mode * c.in_stride + j), fd);
       }
-      uint32_t run_d = d[0], run_n = 1;
+      atomicAdd(&s_hist[w][d], 1u);
+    }
+    const int nvec = (vend - vbeg) >> 2;
+    for (int q0 = threadIdx.x; q0 < nvec; q0 += kHistThreads * 4) {
+      uint4 dv[4];
 #pragma unroll
-      for (int k = 1; k < kHistRun; ++k) {
-        if (k < n) {
-          if (d[k] == run_d) {
+      for (int u = 0; u < 4; ++u) dv[u] = make_uint4(0, 0, 0, 0);
+      for (int f = 0; f < pd.nfields; ++f) {
+        const DigitField fd = pd.f[f];
+        const uint4* col =
+            reinterpret_cast<const uint4*>(c.in + (int64_t)fd.mode * c.in_stride + vbeg);
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = q0 + u * kHistThreads;
+          v[u] = q < nvec ? __ldg(col + q) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          dv[u].x |= field_bits(v[u].x, fd);
+          dv[u].y |= field_bits(v[u].y, fd);
+          dv[u].z |= field_bits(v[u].z, fd);
+          dv[u].w |= field_bits(v[u].w, fd);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (q0 + u * kHistThreads >= nvec) break;
+        const uint32_t e[4] = {dv[u].x, dv[u].y, dv[u].z, dv[u].w};
+        uint32_t run_d = e[0], run_n = 1;
+#pragma unroll
+        for (int k = 1; k < 4; ++k) {
+          if (e[k] == run_d) {
             ++run_n;
           } else {
             atomicAdd(&s_hist[w][run_d], run_n);
-            run_d = d[k];
+            run_d = e[k];
             run_n = 1;
           }
         }
+        atomicAdd(&s_hist[w][run_d], run_n);
       }
-      atomicAdd(&s_hist[w][run_d], run_n);
     }
     __syncthreads();
     for (int dd = threadIdx.x; dd < nbins; dd += kHistThreads) {

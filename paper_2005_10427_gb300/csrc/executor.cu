@@ -220,7 +220,6 @@ qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
       const int32_t* pcols[kMaxOrder];
       for (int i = 0; i < g.prefix_len; ++i)
         pcols[i] = cur.c + (int64_t)g.prefix_modes[i] * cur.stride;
-      QSD_CUDA(cudaMemsetAsync(seg_lb, 0, sizeof(uint32_t) * seg_lookback_words(nnz), st));
       QSD_LAUNCH(tag("seg_discover", gi, -1, nnz, 4 * g.prefix_len),
                  launch_seg_discover(pcols, g.prefix_len, nnz, seg_start, seg_lb, counters,
                                      status, st));

@@ -22,72 +22,105 @@ struct PrefixCols {
   int n;
 };
 
-// One tile of kSegTile entries per block (dynamic tile id, so look-back
-// predecessors are always running). flag[j] = 1 when j starts a bucket
-// (j == 0 or some prefix coordinate differs from entry j-1). The flagged
-// positions are compacted, in order, into seg_start; the last tile appends
-// seg_start[nseg] = nnz and stores nseg.
+// Bucket starts in three steps with no dependency between blocks:
+//   k_seg_count  per tile of kSegTile entries: flag[j] = 1 when j starts a
+//                bucket (j == 0, or a prefix coordinate differs from entry
+//                j-1); the flags are kept as one bit per entry (the warp
+//                ballots) and the tile's count is stored;
+//   k_seg_scan   one block: exclusive prefix of the tile counts, the bucket
+//                count, and the sentinel seg_start[nseg] = nnz;
+//   k_seg_write  per tile: the flagged positions, compacted in order into
+//                seg_start.
+// Each warp covers kSegItems consecutive 32-entry pieces, so the ballot of
+// round i of warp w holds entries [32 * word, 32 * word + 32) where
+// word = tile * kSegTile / 32 + w * kSegItems + i.
 __global__ void __launch_bounds__(kSegThreads)
-k_seg_discover(PrefixCols pc, int nnz, int ntiles, int* __restrict__ seg_start,
-               uint32_t* __restrict__ lb, int* __restrict__ counters,
-               unsigned* status) {
-  __shared__ int s_tile;
-  __shared__ uint32_t s_tmp[kSegWarps + 1];
-  __shared__ uint32_t s_excl;
-  if (threadIdx.x == 0) s_tile = atomicAdd(&counters[kCntSegTile], 1);
-  __syncthreads();
-  const int t = s_tile;
-  if (t >= ntiles) return;
+k_seg_count(PrefixCols pc, int nnz, uint32_t* __restrict__ bits,
+            uint32_t* __restrict__ tile_count) {
+  __shared__ uint32_t s_warp[kSegWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int t = blockIdx.x;
   const int base = t * kSegTile + w * kSegItems * 32;
-  uint32_t ballots[kSegItems];
-  uint32_t wcount = 0;
-#pragma unroll
+  uint32_t cnt = 0;
+  int32_t prev[kMaxOrder];
+  // the entry before this warp's first one
+  for (int m = 0; m < pc.n; ++m) {
+    const int jp = base + lane - 1;
+    prev[m] = (lane == 0 && jp >= 0 && jp < nnz) ? __ldg(pc.col[m] + jp) : 0;
+  }
+#pragma unroll 4
   for (int i = 0; i < kSegItems; ++i) {
     const int j = base + i * 32 + lane;
-    bool flag = false;
-    if (j < nnz) {
-      flag = (j == 0);
-      for (int m = 0; m < pc.n; ++m) {
-        const int32_t* c = pc.col[m];
-        if (j > 0) flag |= __ldg(c + j) != __ldg(c + j - 1);
-      }
+    const bool in = j < nnz;
+    bool flag = in && j == 0;
+    for (int m = 0; m < pc.n; ++m) {
+      const int32_t v = in ? __ldg(pc.col[m] + j) : 0;
+      // entry j-1: lane-1's value, or for lane 0 the previous round's last lane
+      int32_t p = __shfl_up_sync(0xffffffffu, v, 1);
+      const int32_t last = __shfl_sync(0xffffffffu, v, 31);
+      if (lane == 0) p = prev[m];
+      prev[m] = last;
+      flag |= in && j > 0 && v != p;
     }
-    ballots[i] = __ballot_sync(0xffffffffu, flag);
-    wcount += __popc(ballots[i]);
+    const uint32_t bal = __ballot_sync(0xffffffffu, flag);
+    if (lane == 0 && (base + i * 32) < nnz) bits[(base >> 5) + i] = bal;
+    cnt += __popc(bal);
   }
-  // block scan of per-warp counts (lane 0 of each warp contributes)
-  uint32_t total;
-  uint32_t wexcl = block_exclusive_sum<kSegWarps>(lane == 0 ? wcount : 0u, s_tmp, &total);
-  wexcl = __shfl_sync(0xffffffffu, wexcl, 0);
-  // decoupled look-back on the tile totals
-  if (threadIdx.x == 0) {
-    uint32_t excl = 0;
-    if (t == 0) {
-      st_relaxed(lb + t, kLbInclusive | total);
-    } else {
-      st_relaxed(lb + t, kLbAggregate | total);
-      for (int p = t - 1; p >= 0; --p) {
-        uint32_t v = wait_flag(lb + p, status);
-        excl += v & kLbCountMask;
-        if ((v & kLbStateMask) == kLbInclusive) break;
-      }
-      st_relaxed(lb + t, kLbInclusive | (excl + total));
-    }
-    s_excl = excl;
-    if (t == ntiles - 1) {
-      counters[kCntNumSeg] = (int)(excl + total);
-      seg_start[excl + total] = nnz;
-    }
-  }
+  if (lane == 0) s_warp[w] = cnt;
   __syncthreads();
-  uint32_t pos = s_excl + wexcl;
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int k = 0; k < kSegWarps; ++k) tot += s_warp[k];
+    tile_count[t] = tot;
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+k_seg_scan(uint32_t* __restrict__ tile_count, int ntiles, int nnz, int* __restrict__ seg_start,
+           int* __restrict__ counters) {
+  __shared__ uint32_t s_tmp[33];
+  __shared__ uint32_t s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < ntiles; b0 += 1024) {
+    const int i = b0 + threadIdx.x;
+    const uint32_t v = i < ntiles ? tile_count[i] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_exclusive_sum<32>(v, s_tmp, &total);
+    const uint32_t carry = s_carry;
+    if (i < ntiles) tile_count[i] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry = carry + total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    counters[kCntNumSeg] = (int)s_carry;
+    seg_start[s_carry] = nnz;
+  }
+}
+
+__global__ void __launch_bounds__(kSegThreads)
+k_seg_write(int nnz, const uint32_t* __restrict__ bits, const uint32_t* __restrict__ tile_off,
+            int* __restrict__ seg_start) {
+  __shared__ uint32_t s_tmp[kSegWarps + 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int t = blockIdx.x;
+  const int base = t * kSegTile + w * kSegItems * 32;
+  uint32_t bal[kSegItems], cnt = 0;
+#pragma unroll
+  for (int i = 0; i < kSegItems; ++i) {
+    bal[i] = (base + i * 32) < nnz ? bits[(base >> 5) + i] : 0u;
+    cnt += __popc(bal[i]);
+  }
+  uint32_t total;
+  uint32_t wexcl = block_exclusive_sum<kSegWarps>(lane == 0 ? cnt : 0u, s_tmp, &total);
+  wexcl = __shfl_sync(0xffffffffu, wexcl, 0);
+  uint32_t pos = tile_off[t] + wexcl;
   const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
   for (int i = 0; i < kSegItems; ++i) {
-    if (ballots[i] >> lane & 1u)
-      seg_start[pos + __popc(ballots[i] & lt)] = base + i * 32 + lane;
-    pos += __popc(ballots[i]);
+    if (bal[i] >> lane & 1u) seg_start[pos + __popc(bal[i] & lt)] = base + i * 32 + lane;
+    pos += __popc(bal[i]);
   }
 }
 
@@ -164,17 +197,25 @@ cudaError_t launch_seg_discover(const int32_t* const* prefix_cols, int nprefix,
                                 int nnz, int* seg_start, uint32_t* seg_lb,
                                 int* counters, unsigned* status,
                                 cudaStream_t stream) {
+  (void)status;
   PrefixCols pc;
   pc.n = nprefix;
   for (int m = 0; m < kMaxOrder; ++m) pc.col[m] = m < nprefix ? prefix_cols[m] : nullptr;
   const int ntiles = (nnz + kSegTile - 1) / kSegTile;
   if (ntiles == 0) return cudaSuccess;
-  k_seg_discover<<<ntiles, kSegThreads, 0, stream>>>(pc, nnz, ntiles, seg_start,
-                                                      seg_lb, counters, status);
+  // seg_lb holds the tile counts (ntiles words) followed by the flag bits
+  uint32_t* tile_count = seg_lb;
+  uint32_t* bits = seg_lb + ntiles + 1;
+  k_seg_count<<<ntiles, kSegThreads, 0, stream>>>(pc, nnz, bits, tile_count);
+  k_seg_scan<<<1, 1024, 0, stream>>>(tile_count, ntiles, nnz, seg_start, counters);
+  k_seg_write<<<ntiles, kSegThreads, 0, stream>>>(nnz, bits, tile_count, seg_start);
   return cudaGetLastError();
 }
 
-int seg_lookback_words(int nnz) { return (nnz + kSegTile - 1) / kSegTile + 1; }
+// Words of scratch for bucket discovery: tile counts, then one bit per entry.
+int seg_lookback_words(int nnz) {
+  return (nnz + kSegTile - 1) / kSegTile + 1 + (nnz + 31) / 32 + kSegItems;
+}
 
 cudaError_t launch_seg_classify(const int* seg_start, int* counters, int nnz, int small_max,
                                 int chunk, int2* large, int* chunk_base, int* group_base,
