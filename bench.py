@@ -201,6 +201,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
     ap.add_argument("--check", action="store_true", help="sampled parity check vs the oracle")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 256-tensor batched-vs-single-calls measurement")
+    ap.add_argument("--no-tune", action="store_true", help="batched run without autotuning")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the Poisson-stream serving measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -321,6 +326,21 @@ def main():
                "h2d_bytes_per_step": len(plans) * nnz * R,
                "d2h_bytes_per_step": len(plans) * nnz * R}
 
+    batched = None
+    if not args.no_batched:
+        del cb, vbuf
+        batched = bench_batched(qsd, dev, stream, steps=max(5, min(args.steps, 20)),
+                                warmup=args.warmup, tune=not args.no_tune)
+        cb = [torch.empty((r, nnz), dtype=torch.int32, device=dev) for _ in range(2)]
+        vbuf = [torch.empty(nnz, dtype=t.vals.dtype, device=dev) for _ in range(2)]
+
+    serving = None
+    if not args.no_serving and rank == 0:
+        del cb, vbuf
+        serving = bench_serving(qsd, dev)
+        cb = [torch.empty((r, nnz), dtype=torch.int32, device=dev) for _ in range(2)]
+        vbuf = [torch.empty(nnz, dtype=t.vals.dtype, device=dev) for _ in range(2)]
+
     check = None
     if args.check:
         check = sampled_check(qsd, t, plans, perms, cb, vbuf, ws, stream)
@@ -347,12 +367,185 @@ def main():
                                 "share": round(a["ms"] / total_ms, 4) if total_ms else None}
                             for k, a in sorted(agg.items(), key=lambda kv: -kv[1]["ms"])},
                 "clocks": clocks}
+        if batched is not None:
+            line["batched"] = batched
+        if serving is not None:
+            line["serving"] = serving
         if check is not None:
             line["check"] = check
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def bench_batched(qsd, dev, stream, steps: int, warmup: int, tune: bool = True):
+    """The batched workload: 256 tensors (orders 3-5, log-uniform sizes in
+    [1e3, 4e6] and dims in [100, 1e6], Zipf 1.1, float32 values, identity
+    input order, a random non-identity target each) transposed by one graph
+    launch per step, against the same tensors as back-to-back single calls;
+    every output of both is compared bit for bit."""
+    descs = synth.batch_workload()
+    tens = [synth.gen_coo(d["dims"], d["nnz"], d["dists"], d["val_kind"], d["seed"], dev)
+            for d in descs]
+    plans = [qsd.Plan(d["dims"], d["perm"]) for d in descs]
+    outs = [([torch.empty_like(t.coords) for _ in range(2)],
+             [torch.empty_like(t.vals) for _ in range(2)]) for t in tens]
+    batch = qsd.Batch([(p, t.coords, t.vals, o[0], o[1]) for p, t, o in zip(plans, tens, outs)])
+    total = sum(t.nnz for t in tens)
+    R_bytes = sum(t.nnz * (4 * t.order + t.vals.element_size()) for t in tens)
+    ws = torch.empty(batch.workspace_bytes(), dtype=torch.uint8, device=dev)
+    tuned, tune_s = None, None
+    if tune:
+        big = torch.empty(max(2 * batch.workspace_bytes(), batch.workspace_bytes() + (1 << 30)),
+                          dtype=torch.uint8, device=dev)
+        t0 = time.perf_counter()
+        tuned = batch.tune(big, reps=2, stream=stream)
+        tune_s = time.perf_counter() - t0
+        del big
+        ws = torch.empty(batch.workspace_bytes(), dtype=torch.uint8, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(warmup):
+        batch.run(ws, stream)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        batch.run(ws, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = ev0.elapsed_time(ev1) / steps
+    if qsd.workspace_status(ws, stream) != 0:
+        raise SystemExit("device status set by the batched run")
+
+    # the same tensors as single calls, one after another on the stream
+    souts = [([torch.empty_like(t.coords) for _ in range(2)],
+              [torch.empty_like(t.vals) for _ in range(2)]) for t in tens]
+    sws = torch.empty(max(p.workspace_bytes(t.nnz) for p, t in zip(plans, tens)),
+                      dtype=torch.uint8, device=dev)
+    sels = [0] * len(tens)
+
+    def singles():
+        for i, (p, t, o) in enumerate(zip(plans, tens, souts)):
+            sels[i] = qsd.transpose_from(t.coords, t.vals, o[0], o[1], t.nnz, p, sws, stream)
+
+    for _ in range(warmup):
+        singles()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        singles()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = ev0.elapsed_time(ev1) / steps
+    same = all(torch.equal(outs[i][0][batch.result(i)], souts[i][0][sels[i]]) and
+               torch.equal(outs[i][1][batch.result(i)].view(torch.int32),
+                           souts[i][1][sels[i]].view(torch.int32)) for i in range(len(tens)))
+    peak, _ = measured_peaks()
+    return {"workload": "batch256_r3-5_nnz1e3-4e6_zipf1.1_f32", "tensors": len(tens),
+            "nnz_total": total, "steps": steps, "warmup": warmup,
+            "batched": {"value": round(total / (ms_b / 1e3) / 1e9, 3), "unit": "Gnnz/s",
+                        "ms_per_step": round(ms_b, 4), "graph_launches_per_step": 1,
+                        "min_traffic_frac": round(2 * R_bytes / (ms_b / 1e3) / 1e9 / peak, 4)},
+            "single_calls": {"value": round(total / (ms_s / 1e3) / 1e9, 3), "unit": "Gnnz/s",
+                             "ms_per_step": round(ms_s, 4)},
+            "speedup": round(ms_s / ms_b, 3), "identical_outputs": bool(same),
+            "tuned_options": tuned, "tune_seconds": None if tune_s is None else round(tune_s, 2)}
+
+
+def bench_serving(qsd, dev, budget_gb: float = 40.0, n_requests: int = 10_000,
+                  rate: float = 2000.0, check_every: int = 200):
+    """The serving workload: a resident pool of 64 tensors (orders 3-4,
+    log-uniform sizes in [1e4, 5e7], Zipf 1.2, float64 values) and 10k
+    requests arriving as a Poisson stream at 2k/s, each a random non-identity
+    target order of a random pool tensor, served under a 40 GB budget by the
+    continuous-batching server. Latency = arrival to completion on the device.
+    Every check_every-th result is compared bit for bit with the standalone
+    transposition of the same request (alone vs in the mix)."""
+    pool_desc, reqs = synth.serving_workload(n_requests=n_requests, rate=rate)
+    t0 = time.perf_counter()
+    pool = [synth.gen_coo(d["dims"], d["nnz"], d["dists"], d["val_kind"], d["seed"], dev)
+            for d in pool_desc]
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    srv = qsd.Server(int(budget_gb * (1 << 30)), val_bytes=8, streams=2, max_batch=256)
+    ids = [srv.add_tensor(t.coords, t.vals, t.dims) for t in pool]
+    # warm-up: a few requests per order (plans, code paths), not timed
+    for i in range(min(8, len(pool))):
+        srv.submit(ids[i], list(reversed(range(pool[i].order))))
+    warm = 0
+    while warm < min(8, len(pool)):
+        for r in srv.poll(64, wait_ms=100):
+            srv.release(r["request"])
+            warm += 1
+    clock = qsd.server_clock
+    start = clock() + 0.05
+    lat, entries, done_t, first_arrival = [], 0, [], None
+    kept = {}
+    rid_of = {}
+    errors = []
+
+    def driver():
+        for k, (off, i, perm) in enumerate(reqs):
+            target = start + off
+            while True:
+                dt = target - clock()
+                if dt <= 0:
+                    break
+                time.sleep(dt - 0.0002 if dt > 0.0005 else 0)
+            rid_of[srv.submit(ids[i], perm, arrival_s=target)] = k
+
+    th = threading.Thread(target=driver)
+    th.start()
+    got = 0
+    while got < len(reqs):
+        for r in srv.poll(512, wait_ms=20):
+            got += 1
+            if r["status"] != 0:
+                errors.append(r["status"])
+                srv.release(r["request"])
+                continue
+            lat.append(r["done_s"] - r["arrival_s"])
+            done_t.append(r["done_s"])
+            entries += r["nnz"]
+            while r["request"] not in rid_of and th.is_alive():
+                time.sleep(0.0001)
+            k = rid_of.get(r["request"], -1)
+            if k >= 0 and k % check_every == 0:
+                t = pool[reqs[k][1]]
+                oc = torch.empty_like(t.coords)
+                ov = torch.empty_like(t.vals)
+                srv.copy_result(r["request"], oc, ov)
+                torch.cuda.current_stream().synchronize()  # copied before the memory is reused
+                kept[k] = (oc, ov)
+            srv.release(r["request"])
+        if not th.is_alive() and got < len(reqs) and time.perf_counter() - t0 > 600:
+            break
+    th.join()
+    torch.cuda.synchronize()
+    stats = srv.stats()
+    srv.close()
+    same = True
+    for k, (oc, ov) in kept.items():
+        _, i, perm = reqs[k]
+        c, v = qsd.transpose(pool[i].coords.clone(), pool[i].vals.clone(),
+                             qsd.Plan(pool[i].dims, perm))
+        same &= bool(torch.equal(c, oc) and torch.equal(v.view(torch.int64), ov.view(torch.int64)))
+    lat_ms = np.array(lat) * 1e3
+    span = max(done_t) - start if done_t else float("nan")
+    offered = sum(pool_desc[i]["nnz"] for _, i, _ in reqs) / reqs[-1][0] / 1e9
+    return {"workload": "serve10k_poisson2000_pool64_r3-4_nnz1e4-5e7_zipf1.2_f64",
+            "requests": len(reqs), "completed": len(lat), "errors": len(errors),
+            "budget_gb": budget_gb, "offered_gnnz_s": round(offered, 3),
+            "value": round(entries / span / 1e9, 3), "unit": "Gnnz/s",
+            "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
+            "mean_ms": round(float(lat_ms.mean()), 3), "max_ms": round(float(lat_ms.max()), 3),
+            "steps": stats["steps"], "mean_batch": round(stats["admitted"] / max(stats["steps"], 1), 2),
+            "max_queue_depth": stats["max_queue_depth"],
+            "max_inflight": stats["max_inflight_seen"],
+            "peak_budget_gb": round(stats["peak_bytes"] / (1 << 30), 3),
+            "alone_vs_mix_checked": len(kept), "alone_vs_mix_identical": bool(same),
+            "pool_gen_seconds": round(gen_s, 1)}
 
 
 def sampled_check(qsd, t, plans, perms, cb, vbuf, ws, stream):

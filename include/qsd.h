@@ -90,6 +90,11 @@ typedef struct {
   int no_skip;           /* nonzero: ignore the input ordering and run a full
                             radix sort over every mode (the baseline of
                             Section 3 that the method improves on) */
+  int tile;              /* entries a global pass stages in shared memory at
+                            once: 1024, 2048 or 4096 (smaller when the rows
+                            do not fit); 0 = automatic */
+  int chunk_tiles;       /* tiles per chunk, the unit of the per-chunk digit
+                            counts, 1..256; 0 = automatic (8) */
 } qsd_plan_options;
 
 /* Description of a plan (qsd_plan_get_info). */
@@ -224,6 +229,189 @@ qsd_status qsd_workspace_status(const void* workspace, void* stream,
 /* Waits for `stream`, then returns and clears the current device's sticky
  * status word, which every transpose on that device ORs its errors into. */
 qsd_status qsd_get_async_status(void* stream, qsd_status* out);
+
+/* ---- Batches ----
+ * Many independent tensors transposed together. The paper transposes one
+ * tensor at a time; a batch runs the same method (each tensor gets its own
+ * plan and result, bit for bit the result qsd_transpose gives) but shares
+ * the launches among the tensors: each stage (bucket discovery, bucket
+ * sort, and every radix pass's count, offset and move kernels) is one
+ * launch of persistent thread blocks that take work items of every tensor
+ * at that stage. Tensors whose plans have several groups run them in
+ * rounds; a tensor with fewer passes drops out of the later passes. The
+ * whole launch sequence is captured once in a CUDA graph and replayed by
+ * each qsd_batch_run (one graph launch per run).
+ *
+ * A batch binds its buffers at creation: each tensor's input is read-only
+ * and its result goes to its own double buffer, so a batch can be run any
+ * number of times (each run recomputes the same results). */
+typedef struct qsd_batch_s* qsd_batch_t;
+
+/* One tensor of a batch. All pointers are device memory. */
+typedef struct {
+  qsd_plan_t plan;       /* its plan (copied by qsd_batch_create) */
+  int64_t nnz;           /* entries, >= 0 */
+  const int32_t* in;     /* input rows, mode m at in + m * in_stride, sorted
+                            under the plan's input order; read only */
+  int64_t in_stride;     /* >= nnz */
+  const void* in_vals;   /* input values (val_bytes each); NULL when the
+                            batch carries no values */
+  int32_t* out[2];       /* result double buffer, mode m at
+                            out[s] + m * out_stride; must not overlap `in` */
+  int64_t out_stride;    /* >= nnz */
+  void* out_vals[2];     /* value double buffer (NULL without values) */
+} qsd_batch_item;
+
+/* Execution options of a batch (zero-initialise for defaults). digit_bits
+ * and local_capacity replace every plan's own when nonzero; tile and
+ * chunk_tiles are as in qsd_plan_options. */
+typedef struct {
+  int digit_bits;      /* 0 = each plan's own */
+  int local_capacity;  /* 0 = 4096 */
+  int tile;            /* 0 = automatic */
+  int chunk_tiles;     /* 0 = 8 */
+  int no_graph;        /* nonzero: launch directly instead of replaying a graph */
+  int use_tuned;       /* nonzero: take the options the tuning cache holds for
+                          a batch of this shape, if any (qsd_batch_tune) */
+} qsd_batch_options;
+
+/* Creates a batch of n >= 1 tensors. val_bytes is 0 (no values), 4 or 8 for
+ * every tensor. opts may be NULL. Checks every item (plans, strides,
+ * pointers, total entries below 2^30) and uploads the batch's work tables
+ * to the device (synchronously). Errors: QSD_ERR_INVALID_ARGUMENT,
+ * QSD_ERR_UNSUPPORTED, QSD_ERR_OUT_OF_MEMORY, QSD_ERR_CUDA. */
+qsd_status qsd_batch_create(const qsd_batch_item* items, int n, int val_bytes,
+                            const qsd_batch_options* opts, qsd_batch_t* out);
+
+/* Device scratch (bytes) qsd_batch_run needs. */
+qsd_status qsd_batch_workspace_bytes(qsd_batch_t batch, size_t* bytes);
+
+/* Transposes every tensor of the batch on `stream`. workspace: device
+ * memory of at least qsd_batch_workspace_bytes bytes, 256-byte aligned; its
+ * first word is the status word qsd_workspace_status reads. The first run
+ * with a given workspace captures the graph (not on `stream` itself); later
+ * runs replay it. A batch is not safe to run from two host threads at once.
+ * Errors: QSD_ERR_WORKSPACE_TOO_SMALL, QSD_ERR_INVALID_ARGUMENT,
+ * QSD_ERR_CUDA (nothing enqueued on an argument error). */
+qsd_status qsd_batch_run(qsd_batch_t batch, void* workspace, size_t workspace_bytes,
+                         void* stream);
+
+/* Which buffer of item i's double buffer holds its result after a run. */
+qsd_status qsd_batch_result(qsd_batch_t batch, int i, int* selector);
+
+/* The options the batch runs with. */
+qsd_status qsd_batch_get_options(qsd_batch_t batch, qsd_batch_options* out);
+
+/* Autotuner. Times qsd_batch_run under candidate options (tile size, digit
+ * width, shared-memory bucket capacity, chunk length; coordinate search from
+ * the current options, `reps` timed runs each, CUDA events on `stream`),
+ * keeps the fastest, stores it in the process's tuning cache under the
+ * batch's shape and writes it to *best (may be NULL). Candidates whose
+ * workspace exceeds workspace_bytes are skipped. Synchronises `stream`. */
+qsd_status qsd_batch_tune(qsd_batch_t batch, void* workspace, size_t workspace_bytes,
+                          void* stream, int reps, qsd_batch_options* best);
+
+/* Writes / reads the tuning cache as text (one shape and its options per
+ * line); loading adds to the cache. */
+qsd_status qsd_tune_cache_save(const char* path);
+qsd_status qsd_tune_cache_load(const char* path);
+
+/* Releases a batch (its device tables and graph). NULL is ignored. */
+void qsd_batch_destroy(qsd_batch_t batch);
+
+/* ---- Serving ----
+ * A request loop over resident tensors (no counterpart in the paper, which
+ * transposes one tensor per call). Callers register tensors that stay in
+ * device memory, then submit requests (tensor, target order) from any host
+ * thread. An engine thread admits queued requests in arrival order while the
+ * in-flight limit and the device memory budget (results and scratch of the
+ * admitted requests) allow, and launches each step's admitted requests as
+ * one batch (qsd_batch_*) on one of several streams: steps overlap on the
+ * device, and requests that arrive while others run join the next step
+ * (continuous batching). Each result is bit for bit the one a single
+ * qsd_transpose call gives. Results stay in the server's memory until
+ * released. Times are seconds of qsd_server_clock(); completion times come
+ * from CUDA events on the device. */
+typedef struct qsd_server_s* qsd_server_t;
+
+typedef struct {
+  size_t memory_budget;    /* device bytes for results and scratch of admitted
+                              requests; reserved when the server is created */
+  int max_inflight;        /* admitted, not yet completed requests (0 = 1024) */
+  int streams;             /* engine streams = steps in flight at once (0 = 2) */
+  int max_batch;           /* requests per step (0 = 256) */
+  int val_bytes;           /* value width of every tensor: 0, 4 or 8 */
+  qsd_batch_options batch; /* execution options of every step (launched
+                              directly; no_graph and use_tuned are ignored) */
+} qsd_server_options;
+
+typedef struct {
+  int64_t request;        /* id from qsd_server_submit */
+  int tensor;             /* the request's tensor */
+  int status;             /* qsd_status: QSD_OK, QSD_ERR_BUDGET (the request
+                             alone exceeds the budget; no result), or a device
+                             error recorded during its step */
+  const int32_t* coords;  /* device: result rows, mode m at coords + m * stride
+                             (valid until qsd_server_release) */
+  int64_t stride;
+  const void* vals;       /* device: result values (NULL without values) */
+  int64_t nnz;
+  double arrival_s;       /* the request's arrival time */
+  double admit_s;         /* when its step was launched */
+  double done_s;          /* when its step completed on the device */
+} qsd_server_result;
+
+typedef struct {
+  int64_t submitted, admitted, completed, rejected, released, steps;
+  int64_t entries_completed; /* entries transposed by completed requests */
+  int queue_depth, max_queue_depth;
+  int inflight, max_inflight_seen;
+  size_t bytes_in_use, peak_bytes; /* of the budget */
+} qsd_server_stats;
+
+/* Creates a server on the current device and starts its engine thread.
+ * Errors: QSD_ERR_INVALID_ARGUMENT, QSD_ERR_OUT_OF_MEMORY (the budget could
+ * not be reserved), QSD_ERR_CUDA. */
+qsd_status qsd_server_create(const qsd_server_options* opts, qsd_server_t* out);
+
+/* Registers a resident tensor: device rows (mode m at coords + m * stride,
+ * sorted under input_mode_order; NULL = identity) and values, owned by the
+ * caller and kept unchanged while the server lives. *tensor_id receives its
+ * id (0, 1, ...). */
+qsd_status qsd_server_add_tensor(qsd_server_t server, int order, const int64_t* dims,
+                                 const int* input_mode_order, const int32_t* coords,
+                                 int64_t stride, const void* vals, int64_t nnz,
+                                 int* tensor_id);
+
+/* Queues a request to transpose tensor_id into target_perm. arrival_s: its
+ * arrival time (<= 0: now). Never blocks on the device. */
+qsd_status qsd_server_submit(qsd_server_t server, int tensor_id, const int* target_perm,
+                             double arrival_s, int64_t* request_id);
+
+/* Moves up to max_results completed requests (in completion order) into
+ * out, waiting up to wait_ms milliseconds for the first one; *n receives the
+ * count. */
+qsd_status qsd_server_poll(qsd_server_t server, qsd_server_result* out, int max_results,
+                           int wait_ms, int* n);
+
+/* Copies a completed request's result into caller device buffers (rows with
+ * stride dst_stride, values) on `stream`. */
+qsd_status qsd_server_copy_result(qsd_server_t server, int64_t request_id, int32_t* dst_coords,
+                                  int64_t dst_stride, void* dst_vals, void* stream);
+
+/* Returns a completed request's result memory to the budget. A copy made
+ * by qsd_server_copy_result must have completed on its stream first: the
+ * memory can be reused by the next step at once. */
+qsd_status qsd_server_release(qsd_server_t server, int64_t request_id);
+
+qsd_status qsd_server_get_stats(qsd_server_t server, qsd_server_stats* out);
+
+/* Seconds of the monotonic clock the server stamps times with. */
+double qsd_server_clock(void);
+
+/* Stops the engine: queued requests are dropped, steps in flight are waited
+ * for, and all server memory is freed. NULL is ignored. */
+void qsd_server_destroy(qsd_server_t server);
 
 /* ---- Launch profiler (off by default) ----
  * When enabled, every kernel launch of the library on this process is

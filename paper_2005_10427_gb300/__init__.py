@@ -16,8 +16,8 @@ from typing import List, Optional, Sequence, Tuple
 
 from . import _capi
 
-__all__ = ["Plan", "QsdError", "transpose", "transpose_buffers", "transpose_from",
-           "transpose_host", "transpose_noalloc",
+__all__ = ["Plan", "QsdError", "Batch", "Server", "server_clock", "transpose", "transpose_buffers", "transpose_from",
+           "transpose_host", "transpose_noalloc", "tune_cache_save", "tune_cache_load",
            "get_async_status", "workspace_status", "build", "lib", "LIB_PATH"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libqsd.so")
@@ -58,7 +58,8 @@ class Plan:
     def __init__(self, dims: Sequence[int], target_perm: Sequence[int],
                  input_mode_order: Optional[Sequence[int]] = None, *,
                  validate: bool = False, digit_bits: int = 0,
-                 local_capacity: int = 0, no_skip: bool = False):
+                 local_capacity: int = 0, no_skip: bool = False, tile: int = 0,
+                 chunk_tiles: int = 0):
         L = lib()
         r = len(dims)
         self.dims = [int(d) for d in dims]
@@ -67,7 +68,10 @@ class Plan:
         self.input_mode_order = list(range(r)) if input_mode_order is None else \
             [int(x) for x in input_mode_order]
         opts = _capi.PlanOptions(int(bool(validate)), int(digit_bits), int(local_capacity),
-                                 int(bool(no_skip)))
+                                 int(bool(no_skip)), int(tile), int(chunk_tiles))
+        self.options = dict(validate=bool(validate), digit_bits=int(digit_bits),
+                            local_capacity=int(local_capacity), no_skip=bool(no_skip),
+                            tile=int(tile), chunk_tiles=int(chunk_tiles))
         handle = ctypes.c_void_p()
         dims_arr = (ctypes.c_int64 * max(r, 1))(*self.dims)
         st = L.qsd_plan_ex(r, dims_arr, _i32(self.input_mode_order) if r else None,
@@ -197,6 +201,198 @@ def transpose_noalloc(cbuf: Sequence, vbuf: Optional[Sequence], selector: int, n
                                      _stream_handle(stream))
     _check(st, "qsd_transpose_noalloc")
     return int(c.selector)
+
+
+_OPTION_KEYS = ("digit_bits", "local_capacity", "tile", "chunk_tiles", "no_graph",
+                "use_tuned")
+
+
+def _options_dict(o) -> dict:
+    return {k: int(getattr(o, k)) for k in _OPTION_KEYS}
+
+
+class Batch:
+    """Many tensors transposed by one graph launch (qsd_batch_*).
+
+    items: sequence of (plan, in_coords, in_vals, out_cbuf, out_vbuf) where
+    in_coords is an int32 CUDA tensor (r, >= nnz) sorted under the plan's
+    input order, in_vals a value tensor or None, out_cbuf two int32 CUDA
+    tensors (r, >= nnz) and out_vbuf two value tensors or None; nnz is
+    in_coords.shape[1] unless given as a sixth element. The buffers stay bound
+    to the batch (keep them alive). run() recomputes every result; result(i)
+    gives the buffer index holding tensor i's result.
+    """
+
+    def __init__(self, items, *, val_bytes: Optional[int] = None, digit_bits: int = 0,
+                 local_capacity: int = 0, tile: int = 0, chunk_tiles: int = 0,
+                 graph: bool = True, use_tuned: bool = False):
+        L = lib()
+        n = len(items)
+        arr = (_capi.BatchItem * max(n, 1))()
+        vb = val_bytes
+        self._keep = []
+        for i, it in enumerate(items):
+            plan, cin, vin, cout, vout = it[:5]
+            nnz = int(it[5]) if len(it) > 5 else int(cin.shape[1])
+            e = arr[i]
+            e.plan = plan.handle.value
+            e.nnz = nnz
+            e.in_ = cin.data_ptr()
+            e.in_stride = int(cin.stride(0)) if cin.dim() == 2 else nnz
+            e.in_vals = vin.data_ptr() if vin is not None else None
+            e.out[0] = cout[0].data_ptr()
+            e.out[1] = cout[1].data_ptr()
+            e.out_stride = int(cout[0].stride(0)) if cout[0].dim() == 2 else nnz
+            if vout is not None:
+                e.out_vals[0] = vout[0].data_ptr()
+                e.out_vals[1] = vout[1].data_ptr()
+            if vb is None:
+                vb = _val_bytes(vin)
+            self._keep.append(it)
+        opts = _capi.BatchOptions(int(digit_bits), int(local_capacity), int(tile),
+                                  int(chunk_tiles), int(not graph), int(bool(use_tuned)))
+        h = ctypes.c_void_p()
+        _check(L.qsd_batch_create(arr, n, int(vb or 0), ctypes.byref(opts), ctypes.byref(h)),
+               "qsd_batch_create")
+        self._h = h
+        self._lib = L
+        self.n = n
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.qsd_batch_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def workspace_bytes(self) -> int:
+        out = ctypes.c_size_t()
+        _check(self._lib.qsd_batch_workspace_bytes(self._h, ctypes.byref(out)),
+               "qsd_batch_workspace_bytes")
+        return int(out.value)
+
+    def run(self, workspace, stream=None) -> None:
+        _check(self._lib.qsd_batch_run(self._h, ctypes.c_void_p(workspace.data_ptr()),
+                                       int(workspace.numel()), _stream_handle(stream)),
+               "qsd_batch_run")
+
+    def result(self, i: int) -> int:
+        out = ctypes.c_int()
+        _check(self._lib.qsd_batch_result(self._h, int(i), ctypes.byref(out)),
+               "qsd_batch_result")
+        return int(out.value)
+
+    def options(self) -> dict:
+        o = _capi.BatchOptions()
+        _check(self._lib.qsd_batch_get_options(self._h, ctypes.byref(o)),
+               "qsd_batch_get_options")
+        return _options_dict(o)
+
+    def tune(self, workspace, reps: int = 3, stream=None) -> dict:
+        """Autotunes the execution options (qsd_batch_tune); returns the choice."""
+        o = _capi.BatchOptions()
+        _check(self._lib.qsd_batch_tune(self._h, ctypes.c_void_p(workspace.data_ptr()),
+                                        int(workspace.numel()), _stream_handle(stream),
+                                        int(reps), ctypes.byref(o)), "qsd_batch_tune")
+        return _options_dict(o)
+
+
+def server_clock() -> float:
+    """Seconds of the monotonic clock the server stamps times with."""
+    return float(lib().qsd_server_clock())
+
+
+class Server:
+    """Continuous-batching transposition server (qsd_server_*).
+
+    Resident tensors are registered once (add_tensor; keep the tensors
+    alive); submit() queues a request and returns its id; poll() returns
+    completed requests as dicts (status, times, result pointers); copy_result()
+    copies a result into caller tensors; release() returns its memory to the
+    budget.
+    """
+
+    def __init__(self, memory_budget: int, *, val_bytes: int, max_inflight: int = 0,
+                 streams: int = 0, max_batch: int = 0, digit_bits: int = 0,
+                 local_capacity: int = 0, tile: int = 0, chunk_tiles: int = 0):
+        L = lib()
+        bo = _capi.BatchOptions(int(digit_bits), int(local_capacity), int(tile),
+                                int(chunk_tiles), 1, 0)
+        o = _capi.ServerOptions(int(memory_budget), int(max_inflight), int(streams),
+                                int(max_batch), int(val_bytes), bo)
+        h = ctypes.c_void_p()
+        _check(L.qsd_server_create(ctypes.byref(o), ctypes.byref(h)), "qsd_server_create")
+        self._h = h
+        self._lib = L
+        self._tensors = []
+        self.val_bytes = int(val_bytes)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.qsd_server_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def add_tensor(self, coords, vals, dims: Sequence[int],
+                   input_mode_order: Optional[Sequence[int]] = None) -> int:
+        r = coords.shape[0]
+        nnz = int(coords.shape[1])
+        dims_arr = (ctypes.c_int64 * r)(*[int(d) for d in dims])
+        tau = _i32(input_mode_order) if input_mode_order is not None else None
+        out = ctypes.c_int()
+        _check(self._lib.qsd_server_add_tensor(
+            self._h, r, dims_arr, tau, ctypes.c_void_p(coords.data_ptr()),
+            int(coords.stride(0)) if nnz else 0,
+            ctypes.c_void_p(vals.data_ptr()) if vals is not None else None, nnz,
+            ctypes.byref(out)), "qsd_server_add_tensor")
+        self._tensors.append((coords, vals))
+        return int(out.value)
+
+    def submit(self, tensor: int, target_perm: Sequence[int], arrival_s: float = 0.0) -> int:
+        rid = ctypes.c_int64()
+        _check(self._lib.qsd_server_submit(self._h, int(tensor), _i32(target_perm),
+                                           float(arrival_s), ctypes.byref(rid)),
+               "qsd_server_submit")
+        return int(rid.value)
+
+    def poll(self, max_results: int = 256, wait_ms: int = 0) -> List[dict]:
+        arr = (_capi.ServerResult * max(int(max_results), 1))()
+        n = ctypes.c_int()
+        _check(self._lib.qsd_server_poll(self._h, arr, int(max_results), int(wait_ms),
+                                         ctypes.byref(n)), "qsd_server_poll")
+        return [{"request": int(r.request), "tensor": int(r.tensor), "status": int(r.status),
+                 "nnz": int(r.nnz), "coords": r.coords, "vals": r.vals,
+                 "arrival_s": r.arrival_s, "admit_s": r.admit_s, "done_s": r.done_s}
+                for r in arr[:n.value]]
+
+    def copy_result(self, request: int, coords_out, vals_out=None, stream=None) -> None:
+        _check(self._lib.qsd_server_copy_result(
+            self._h, int(request), ctypes.c_void_p(coords_out.data_ptr()),
+            int(coords_out.stride(0)),
+            ctypes.c_void_p(vals_out.data_ptr()) if vals_out is not None else None,
+            _stream_handle(stream)), "qsd_server_copy_result")
+
+    def release(self, request: int) -> None:
+        _check(self._lib.qsd_server_release(self._h, int(request)), "qsd_server_release")
+
+    def stats(self) -> dict:
+        st = _capi.ServerStats()
+        _check(self._lib.qsd_server_get_stats(self._h, ctypes.byref(st)), "qsd_server_get_stats")
+        return {k: int(getattr(st, k)) for k, _ in _capi.ServerStats._fields_}
+
+
+def tune_cache_save(path: str) -> None:
+    _check(lib().qsd_tune_cache_save(os.fsencode(path)), "qsd_tune_cache_save")
+
+
+def tune_cache_load(path: str) -> None:
+    _check(lib().qsd_tune_cache_load(os.fsencode(path)), "qsd_tune_cache_load")
 
 
 def transpose(coords, vals, plan: Plan, *, workspace=None, stream=None):

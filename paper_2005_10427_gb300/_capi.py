@@ -27,7 +27,8 @@ class Values(ctypes.Structure):
 
 class PlanOptions(ctypes.Structure):
     _fields_ = [("validate", ctypes.c_int), ("digit_bits", ctypes.c_int),
-                ("local_capacity", ctypes.c_int), ("no_skip", ctypes.c_int)]
+                ("local_capacity", ctypes.c_int), ("no_skip", ctypes.c_int),
+                ("tile", ctypes.c_int), ("chunk_tiles", ctypes.c_int)]
 
 
 _A = ctypes.c_int * MAX_ORDER
@@ -45,6 +46,43 @@ class ProfileRecord(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_char * 32), ("group", ctypes.c_int), ("pass_", ctypes.c_int),
                 ("entries", ctypes.c_int64), ("algo_bytes", ctypes.c_int64),
                 ("ms", ctypes.c_float)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("nnz", ctypes.c_int64),
+                ("in_", ctypes.c_void_p), ("in_stride", ctypes.c_int64),
+                ("in_vals", ctypes.c_void_p), ("out", ctypes.c_void_p * 2),
+                ("out_stride", ctypes.c_int64), ("out_vals", ctypes.c_void_p * 2)]
+
+
+class BatchOptions(ctypes.Structure):
+    _fields_ = [("digit_bits", ctypes.c_int), ("local_capacity", ctypes.c_int),
+                ("tile", ctypes.c_int), ("chunk_tiles", ctypes.c_int),
+                ("no_graph", ctypes.c_int), ("use_tuned", ctypes.c_int)]
+
+
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
+                ("streams", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("val_bytes", ctypes.c_int), ("batch", BatchOptions)]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("request", ctypes.c_int64), ("tensor", ctypes.c_int), ("status", ctypes.c_int),
+                ("coords", ctypes.c_void_p), ("stride", ctypes.c_int64),
+                ("vals", ctypes.c_void_p), ("nnz", ctypes.c_int64),
+                ("arrival_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("released", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("entries_completed", ctypes.c_int64),
+                ("queue_depth", ctypes.c_int), ("max_queue_depth", ctypes.c_int),
+                ("inflight", ctypes.c_int), ("max_inflight_seen", ctypes.c_int),
+                ("bytes_in_use", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t)]
 
 
 # (name, restype, argtypes) for every entry point of include/qsd.h
@@ -67,6 +105,25 @@ SIGNATURES = [
                                ctypes.POINTER(Values), P, ctypes.c_size_t, P]),
     ("qsd_workspace_status", I, [P, P, ctypes.POINTER(I)]),
     ("qsd_get_async_status", I, [P, ctypes.POINTER(I)]),
+    ("qsd_batch_create", I, [ctypes.POINTER(BatchItem), I, I, ctypes.POINTER(BatchOptions),
+                             ctypes.POINTER(P)]),
+    ("qsd_batch_workspace_bytes", I, [P, ctypes.POINTER(ctypes.c_size_t)]),
+    ("qsd_batch_run", I, [P, P, ctypes.c_size_t, P]),
+    ("qsd_batch_result", I, [P, I, ctypes.POINTER(I)]),
+    ("qsd_batch_get_options", I, [P, ctypes.POINTER(BatchOptions)]),
+    ("qsd_batch_tune", I, [P, P, ctypes.c_size_t, P, I, ctypes.POINTER(BatchOptions)]),
+    ("qsd_tune_cache_save", I, [ctypes.c_char_p]),
+    ("qsd_tune_cache_load", I, [ctypes.c_char_p]),
+    ("qsd_batch_destroy", None, [P]),
+    ("qsd_server_create", I, [ctypes.POINTER(ServerOptions), ctypes.POINTER(P)]),
+    ("qsd_server_add_tensor", I, [P, I, P, P, P, I64, P, I64, ctypes.POINTER(I)]),
+    ("qsd_server_submit", I, [P, I, P, ctypes.c_double, ctypes.POINTER(I64)]),
+    ("qsd_server_poll", I, [P, ctypes.POINTER(ServerResult), I, I, ctypes.POINTER(I)]),
+    ("qsd_server_copy_result", I, [P, I64, P, I64, P, P]),
+    ("qsd_server_release", I, [P, I64]),
+    ("qsd_server_get_stats", I, [P, ctypes.POINTER(ServerStats)]),
+    ("qsd_server_clock", ctypes.c_double, []),
+    ("qsd_server_destroy", None, [P]),
     ("qsd_profile_enable", I, [I]),
     ("qsd_profile_read", I, [ctypes.POINTER(ProfileRecord), I, ctypes.POINTER(I)]),
     ("qsd_profile_reset", I, []),

@@ -167,15 +167,33 @@ __device__ __forceinline__ void group_sync() {
   }
 }
 
+// True on every participant when `pred` holds on all of the first NTHREADS
+// threads (named barrier BAR with an AND reduction): a group that must leave
+// a loop together decides it here.
+template <int BAR, int NTHREADS>
+__device__ __forceinline__ bool group_all(bool pred) {
+  unsigned r;
+  asm volatile(
+      "{ .reg .pred q, r; setp.ne.u32 q, %1, 0; bar.red.and.pred r, %2, %3, q; "
+      "selp.u32 %0, 1, 0, r; }"
+      : "=r"(r)
+      : "r"((unsigned)pred), "n"(BAR), "n"(NTHREADS)
+      : "memory");
+  return r != 0;
+}
+
 // Counts fit 16 bits (a tile has at most 65535 entries). With BAR != 0 the
 // ranking threads are the first NWARPS warps of the block and synchronise on
 // named barrier BAR only (other warps of the block may be doing other work).
+// Returns whether `ok` held on every ranking thread (reduced at the ranking's
+// first barrier, so a group can agree to stop at no extra cost).
 template <int NWARPS, int ITEMS, int BAR = 0>
-__device__ __forceinline__ void block_rank(const uint32_t (&dig)[ITEMS],
+__device__ __forceinline__ bool block_rank(const uint32_t (&dig)[ITEMS],
                                            uint32_t (&rank)[ITEMS],
                                            uint16_t* s_warp_hist,  // [NWARPS][kRadix]
                                            uint32_t* s_bin_start,  // [kRadix]
-                                           uint32_t* s_bin_count)  // [kRadix]
+                                           uint32_t* s_bin_count,  // [kRadix]
+                                           bool ok = true)
 {
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
@@ -205,7 +223,11 @@ __device__ __forceinline__ void block_rank(const uint32_t (&dig)[ITEMS],
     const uint32_t o = __shfl_sync(0xffffffffu, old[i], __ffs(peers[i]) - 1);
     rank[i] = ((o >> ((dig[i] & 1u) * 16)) & 0xffffu) + __popc(peers[i] & lt);
   }
-  group_sync<BAR, NWARPS * 32>();
+  bool all_ok;
+  if constexpr (BAR == 0)
+    all_ok = __syncthreads_and(ok) != 0;
+  else
+    all_ok = group_all<BAR, NWARPS * 32>(ok);
   // exclusive scan over warps for each digit; digit totals
   for (int d = threadIdx.x; d < kRadix; d += NWARPS * 32) {
     uint32_t run = 0;
@@ -245,6 +267,7 @@ __device__ __forceinline__ void block_rank(const uint32_t (&dig)[ITEMS],
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i)
     rank[i] += s_bin_start[dig[i]] + h[dig[i]];
+  return all_ok;
 }
 
 // Block-wide exclusive sum of one value per thread; returns the thread's

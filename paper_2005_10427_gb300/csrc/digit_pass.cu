@@ -23,7 +23,6 @@
 // their bucket), so offsets are computed per bucket.
 #include <cuda_runtime.h>
 
-#include <cstdlib>
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -87,30 +86,51 @@ __device__ __forceinline__ ChunkInfo chunk_info(const LargeSegs& ls, int c) {
   return ci;
 }
 
+// Copies a descriptor word by word (threads t, t + step, ... of a group).
+template <typename D>
+__device__ __forceinline__ void copy_words(D* dst, const D* src, int t, int step) {
+  static_assert(sizeof(D) % 4 == 0, "descriptor of whole words");
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int i = t; i < (int)(sizeof(D) / 4); i += step) d[i] = s[i];
+}
+
 // ---------------------------------------------------------------------------
 // Chunk histograms: 16-byte loads of the digit's rows (four in flight per
 // thread), each vector of four consecutive entries counted into the warp's
 // histogram with one shared atomic per run of equal digits.
 __global__ void __launch_bounds__(kHistThreads)
-k_chunk_hist(Cols c, LargeSegs ls, PassDesc pd, uint32_t* __restrict__ chunk_hist,
-             uint32_t* __restrict__ group_sum, int* __restrict__ claim) {
+k_chunk_hist(const __grid_constant__ PassTensor one, LargeSegs ls,
+             uint32_t* __restrict__ chunk_hist, uint32_t* __restrict__ group_sum,
+             int* __restrict__ claim, PassBatch pb) {
   __shared__ uint32_t s_hist[kHistWarps][kRadix];
   __shared__ int s_chunk;
+  __shared__ PassTensor s_it;  // the chunk's tensor: buffers and digit
   const int w = threadIdx.x >> 5;
-  const int nc = n_chunks(ls);
-  const int nbins = 1 << pd.bits;
-  // vectors line up across the digit's rows when there is one row, or when the
-  // rows are 16-byte aligned and the stride is a multiple of 4 entries
-  const bool vec = pd.nfields == 1 || ((c.in_stride & 3) == 0 &&
-                                       (reinterpret_cast<uintptr_t>(c.in) & 15) == 0);
+  const int nc = pb.t ? pb.counters[kCntPassChunks + pb.pass] : n_chunks(ls);
+  const Cols& c = s_it.c;
+  const PassDesc& pd = s_it.pd;
+  if (!pb.t) copy_words(&s_it, &one, threadIdx.x, kHistThreads);
   while (true) {
     for (int i = threadIdx.x; i < kHistWarps * kRadix; i += kHistThreads)
       (&s_hist[0][0])[i] = 0;
-    if (threadIdx.x == 0) s_chunk = atomicAdd(claim, 1);
+    if (threadIdx.x == 0) {
+      const int idx = atomicAdd(claim, 1);
+      s_chunk = idx < nc ? (pb.t ? pb.chunks[idx] : idx) : -1;
+    }
     __syncthreads();
     const int ch = s_chunk;
-    if (ch >= nc) break;
+    if (ch < 0) break;
     const ChunkInfo ci = chunk_info(ls, ch);
+    if (pb.t) {
+      copy_words(&s_it, pb.t + pb.large_tensor[ci.seg], threadIdx.x, kHistThreads);
+      __syncthreads();
+    }
+    const int nbins = 1 << pd.bits;
+    // vectors line up across the digit's rows when there is one row, or when
+    // the row stride is a multiple of 4 entries (every row then has the same
+    // 16-byte phase)
+    const bool vec = pd.nfields == 1 || (c.in_stride & 3) == 0;
     // Vector path: the digit's rows advance together in 16-byte steps when the
     // row stride is a multiple of 4 entries; entries before the first aligned
     // one and after the last full vector are counted one by one.
@@ -189,12 +209,13 @@ k_chunk_hist(Cols c, LargeSegs ls, PassDesc pd, uint32_t* __restrict__ chunk_his
 // Chunk offsets. One block (kRadix threads, one per digit) per chunk group.
 __global__ void __launch_bounds__(kRadix)
 k_chunk_scan(LargeSegs ls, uint32_t* __restrict__ chunk_hist,
-             const uint32_t* __restrict__ group_sum) {
+             const uint32_t* __restrict__ group_sum, PassBatch pb) {
   __shared__ uint32_t s_tmp[kRadix / 32 + 1];
   const int d = threadIdx.x;
-  const int ng_all = n_groups(ls);
+  const int ng_all = pb.t ? pb.counters[kCntPassGroups + pb.pass] : n_groups(ls);
   const int nc_all = n_chunks(ls);
-  for (int G = blockIdx.x; G < ng_all; G += gridDim.x) {
+  for (int gi = blockIdx.x; gi < ng_all; gi += gridDim.x) {
+    const int G = pb.t ? pb.groups[gi] : gi;
     int s, gb, cb, ng, nc, lo;
     if (ls.single) {
       s = 0;
@@ -277,6 +298,7 @@ struct RowPlan {
 struct TileSlot {
   int chunk, k, ntile, start, end, lo, hi;
   RowPlan row[kMaxRows];
+  PassTensor it;  // the chunk's tensor: buffers and digit
 };
 
 template <int T, int NS, int RW>
@@ -292,6 +314,7 @@ struct WsShared {
   uint32_t bin_count[kRadix];
   uint32_t gbase[2][kRadix];  // destination of sorted position p = gbase[d] + p
   uint32_t invdig[2][T];      // sorted position -> (digit << 16) | tile position
+  int rk_abort;  // the rankers gave up: the writers stop without writing
 };
 
 template <int T>
@@ -316,8 +339,9 @@ __device__ __forceinline__ uintptr_t row_base(const Cols& c, int r) {
 
 template <int T, int NS, int VB, int RW, int WW>
 __global__ void __launch_bounds__(Roles<RW, WW>::kThreads, 1)
-k_digit_move(Cols c, LargeSegs ls, PassDesc pd, const uint32_t* __restrict__ chunk_off,
-             int* __restrict__ claim, unsigned* status) {
+k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls,
+             const uint32_t* __restrict__ chunk_off, int* __restrict__ claim, unsigned* status,
+             PassBatch pb) {
   constexpr int kWsRankWarps = RW, kWsWriteWarps = WW;
   constexpr int kWsRankThreads = Roles<RW, WW>::kRank;
   constexpr int kWsWriteThreads = Roles<RW, WW>::kWrite;
@@ -327,11 +351,9 @@ k_digit_move(Cols c, LargeSegs ls, PassDesc pd, const uint32_t* __restrict__ chu
   extern __shared__ __align__(16) uint8_t smem[];
   WsShared<T, NS, RW>& S = *reinterpret_cast<WsShared<T, NS, RW>*>(smem);
   uint8_t* const stage = smem + ws_header<T, NS, RW>();
-  const size_t bufsz = ws_buffer<T, VB>(c.order);
+  const size_t bufsz = ws_buffer<T, VB>(lay_order);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nchunks = n_chunks(ls);
-  const int nrows = c.order + (VB ? 1 : 0);
-  const int nbins = 1 << pd.bits;
+  const int nchunks = pb.t ? pb.counters[kCntPassChunks + pb.pass] : n_chunks(ls);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
@@ -342,28 +364,51 @@ k_digit_move(Cols c, LargeSegs ls, PassDesc pd, const uint32_t* __restrict__ chu
       mbar_init(&S.ranked[j], kWsRankThreads);
       mbar_init(&S.consumed[j], kWsWriteThreads);
     }
+    S.rk_abort = 0;
   }
   __syncthreads();
 
   if (warp == kWsRankWarps + kWsWriteWarps) {
     // ---------------- producer ----------------
-    int ch = 0, k = 0, ntile = 0;
-    if (lane == 0) ch = atomicAdd(claim, 1);
-    ch = __shfl_sync(0xffffffffu, ch, 0);
+    int ch = 0, k = 0, ntile = 0, issued = 0, drain_from = 0;
+    // the next chunk: an index into the pass's list, -1 when none is left
+    auto claim_chunk = [&]() {
+      int idx = 0;
+      if (lane == 0) idx = atomicAdd(claim, 1);
+      idx = __shfl_sync(0xffffffffu, idx, 0);
+      return idx < nchunks ? (pb.t ? pb.chunks[idx] : idx) : -1;
+    };
+    ch = claim_chunk();
     for (int q = 0;; ++q) {
       const int s = q % NS;
-      if (q >= NS && !mbar_wait(&S.empty[s], ((q / NS) - 1) & 1, status)) break;
+      if (q >= NS) {
+        // lane 0 waits (bounded) and the warp follows its outcome; then every
+        // lane's own wait on the completed phase orders its stores after the
+        // writers' reads of the slot
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait(&S.empty[s], ((q / NS) - 1) & 1, status) ? 1 : 0;
+        if (!__shfl_sync(0xffffffffu, ok, 0)) {
+          drain_from = q - NS;  // tile q - NS (slot s) may still be in flight
+          break;
+        }
+        mbar_wait(&S.empty[s], ((q / NS) - 1) & 1, status);
+      }
       TileSlot& ts = S.slot[s];
       uint8_t* buf = stage + (size_t)s * bufsz;
-      if (ch >= nchunks) {
-        if (lane == 0) ts.chunk = ch;
+      if (ch < 0) {
+        if (lane == 0) ts.chunk = -1;
         __syncwarp();
         mbar_arrive(&S.full[s]);
+        drain_from = q - NS + 1;  // slot s now holds the end marker
         break;
       }
       const ChunkInfo ci = chunk_info(ls, ch);
       ntile = (ci.end - ci.start + T - 1) / T;
       const int start = ci.start + k * T, end = min(start + T, ci.end), n = end - start;
+      copy_words(&ts.it, pb.t ? pb.t + pb.large_tensor[ci.seg] : &one, lane, 32);
+      __syncwarp();
+      const Cols& c = ts.it.c;
+      const int nrows = c.order + (VB ? 1 : 0);
       // row plans: lane r handles row r
       unsigned bytes = 0;
       RowPlan rp;
@@ -424,36 +469,39 @@ k_digit_move(Cols c, LargeSegs ls, PassDesc pd, const uint32_t* __restrict__ chu
                  reinterpret_cast<const void*>(row_base(c, lane) + (uintptr_t)(start + rp.head) * e),
                  bytes, &S.full[s]);
       }
+      ++issued;
       // next work item
       if (++k >= ntile) {
         k = 0;
-        if (lane == 0) ch = atomicAdd(claim, 1);
-        ch = __shfl_sync(0xffffffffu, ch, 0);
+        ch = claim_chunk();
       }
     }
+    // The block exits only after the bulk copies it started have landed: on
+    // a normal end these waits return at once; after a timeout elsewhere they
+    // are bounded like every other wait.
+    if (lane == 0)
+      for (int x = drain_from > 0 ? drain_from : 0; x < issued; ++x)
+        mbar_wait(&S.full[x % NS], (x / NS) & 1, status);
   } else if (warp < kWsRankWarps) {
     // ---------------- rankers ----------------
     const int w = warp;
     for (int q = 0;; ++q) {
       const int s = q % NS, j = q & 1;
-      const bool ok = mbar_wait(&S.full[s], (q / NS) & 1, status);
+      const bool okf = mbar_wait(&S.full[s], (q / NS) & 1, status);
+      const bool okc = q < 2 || mbar_wait(&S.consumed[j], ((q / 2) - 1) & 1, status);
+      if (!(okf && okc)) S.rk_abort = 1;  // the writers stop without writing
       const TileSlot& ts = S.slot[s];
-      const int ch = ts.chunk;
-      if (q >= 2 && !mbar_wait(&S.consumed[j], ((q / 2) - 1) & 1, status)) break;
-      if (ch >= nchunks || !ok) {
-        mbar_arrive(&S.ranked[j]);  // the writers see the end marker too
-        break;
-      }
+      // go: a tile to rank. The rankers share named barrier 1, so they agree
+      // on it (at the ranking's first barrier) before any of them leaves.
+      const bool go = okf && okc && ts.chunk >= 0;
       const uint8_t* buf = stage + (size_t)s * bufsz;
-      const int n_valid = ts.end - ts.start;
-      if (ts.k == 0)  // a new chunk: its first output slot per digit
-        for (int d = threadIdx.x; d < nbins; d += kWsRankThreads)
-          S.off[d] = chunk_off[(size_t)ch * kRadix + d];
+      const int n_valid = go ? ts.end - ts.start : 0;
       uint32_t dig[ITEMS], rank[ITEMS];
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) dig[i] = 0;
-      for (int f = 0; f < pd.nfields; ++f) {
-        const DigitField fd = pd.f[f];
+      const int nf = go ? ts.it.pd.nfields : 0;
+      for (int f = 0; f < nf; ++f) {
+        const DigitField fd = ts.it.pd.f[f];
         const uint32_t* row = reinterpret_cast<const uint32_t*>(
             buf + (size_t)fd.mode * row_slot<T>(4) + ts.row[fd.mode].off);
 #pragma unroll
@@ -465,7 +513,16 @@ k_digit_move(Cols c, LargeSegs ls, PassDesc pd, const uint32_t* __restrict__ chu
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i)
         if (w * ITEMS * 32 + i * 32 + lane >= n_valid) dig[i] = kRadix - 1;  // padding sorts last
-      block_rank<RW, ITEMS, 1>(dig, rank, S.warp_hist, S.bin_start, S.bin_count);
+      if (!block_rank<RW, ITEMS, 1>(dig, rank, S.warp_hist, S.bin_start, S.bin_count, go)) {
+        mbar_arrive(&S.ranked[j]);  // the writers see the end marker (or the abort)
+        break;
+      }
+      const int ch = ts.chunk;
+      const PassDesc& pd = ts.it.pd;
+      const int nbins = 1 << pd.bits;
+      if (ts.k == 0)  // a new chunk: its first output slot per digit
+        for (int d = threadIdx.x; d < nbins; d += kWsRankThreads)
+          S.off[d] = chunk_off[(size_t)ch * kRadix + d];
       for (int d = threadIdx.x; d < nbins; d += kWsRankThreads) {
         uint32_t cnt = S.bin_count[d];
         if (d == kRadix - 1) cnt -= (uint32_t)(T - n_valid);
@@ -485,8 +542,9 @@ k_digit_move(Cols c, LargeSegs ls, PassDesc pd, const uint32_t* __restrict__ chu
       const int s = q % NS, j = q & 1;
       if (!mbar_wait(&S.ranked[j], (q / 2) & 1, status)) break;
       const TileSlot& ts = S.slot[s];
-      if (ts.chunk >= nchunks) break;
+      if (ts.chunk < 0 || S.rk_abort) break;
       const uint8_t* buf = stage + (size_t)s * bufsz;
+      const Cols& c = ts.it.c;
       const int n_valid = ts.end - ts.start, lo = ts.lo, hi = ts.hi;
       int dst_pos[WITEMS], src_idx[WITEMS];
 #pragma unroll
@@ -533,7 +591,7 @@ size_t ws_smem(int order) {
 template <int T, int NS, int VB, int RW, int WW>
 cudaError_t launch_move_t(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
                           const uint32_t* chunk_off, int* claim, int max_chunks,
-                          unsigned* status, cudaStream_t stream) {
+                          unsigned* status, const PassBatch& pb, cudaStream_t stream) {
   const size_t smem = ws_smem<T, NS, VB, RW>(c.order);
   cudaError_t e = cudaFuncSetAttribute(k_digit_move<T, NS, VB, RW, WW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -541,55 +599,32 @@ cudaError_t launch_move_t(const Cols& c, const LargeSegs& ls, const PassDesc& pd
   int grid = sm_count();
   if (grid > max_chunks) grid = max_chunks;
   if (grid < 1) grid = 1;
+  PassTensor one;
+  one.c = c;
+  one.pd = pd;
   k_digit_move<T, NS, VB, RW, WW><<<grid, Roles<RW, WW>::kThreads, smem, stream>>>(
-      c, ls, pd, chunk_off, claim, status);
+      one, c.order, ls, chunk_off, claim, status, pb);
   return cudaGetLastError();
 }
 
-// Staging slots wanted for 2048-entry tiles (QSD_NS=3..5; default 3).
-int ws_slots() {
-  if (const char* e = getenv("QSD_NS")) {
-    const int v = atoi(e);
-    return v < 3 ? 3 : (v > 5 ? 5 : v);
-  }
-  return 3;
-}
-
-// Warps per role (QSD_WS=8 for 8+8, 16 for 16+15; default 16).
-int ws_width() {
-  if (const char* e = getenv("QSD_WS")) return atoi(e) == 8 ? 8 : 16;
-  return 16;
-}
-
 // Ring depth for a tile size: three staging buffers when they fit 227 KB of
-// shared memory, else two.
+// shared memory, else two. Tiles of 4096 and 2048 entries use 16 ranking and
+// 15 writing warps, tiles of 1024 entries 8 and 8.
 template <int VB>
 cudaError_t launch_move_vb(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
                            const uint32_t* chunk_off, int* claim, int max_chunks,
-                           unsigned* status, cudaStream_t stream) {
+                           unsigned* status, const PassBatch& pb, cudaStream_t stream) {
   constexpr size_t kMax = 227 * 1024;
 #define QSD_MV(T_, NS_, RW_, WW_)                                                      \
   return launch_move_t<T_, NS_, VB, RW_, WW_>(c, ls, pd, chunk_off, claim, max_chunks, status, \
-                                              stream)
-  const bool wide = ws_width() == 16;
+                                              pb, stream)
   if (ls.tile == 4096) {
-    if (wide) {
-      if (ws_smem<4096, 3, VB, 16>(c.order) <= kMax) QSD_MV(4096, 3, 16, 15);
-      QSD_MV(4096, 2, 16, 15);
-    }
-    if (ws_smem<4096, 3, VB, 8>(c.order) <= kMax) QSD_MV(4096, 3, 8, 8);
-    QSD_MV(4096, 2, 8, 8);
+    if (ws_smem<4096, 3, VB, 16>(c.order) <= kMax) QSD_MV(4096, 3, 16, 15);
+    QSD_MV(4096, 2, 16, 15);
   }
   if (ls.tile == 2048) {
-    if (wide) {
-      const int ns = ws_slots();
-      if (ns >= 5 && ws_smem<2048, 5, VB, 16>(c.order) <= kMax) QSD_MV(2048, 5, 16, 15);
-      if (ns >= 4 && ws_smem<2048, 4, VB, 16>(c.order) <= kMax) QSD_MV(2048, 4, 16, 15);
-      if (ws_smem<2048, 3, VB, 16>(c.order) <= kMax) QSD_MV(2048, 3, 16, 15);
-      QSD_MV(2048, 2, 16, 15);
-    }
-    if (ws_smem<2048, 3, VB, 8>(c.order) <= kMax) QSD_MV(2048, 3, 8, 8);
-    QSD_MV(2048, 2, 8, 8);
+    if (ws_smem<2048, 3, VB, 16>(c.order) <= kMax) QSD_MV(2048, 3, 16, 15);
+    QSD_MV(2048, 2, 16, 15);
   }
   if (ws_smem<1024, 3, VB, 8>(c.order) <= kMax) QSD_MV(1024, 3, 8, 8);
   QSD_MV(1024, 2, 8, 8);
@@ -598,58 +633,59 @@ cudaError_t launch_move_vb(const Cols& c, const LargeSegs& ls, const PassDesc& p
 
 }  // namespace
 
-// Entries per tile: the largest of 4096, 2048, 1024 whose two-slot ring fits
-// 227 KB of shared memory (QSD_TILE overrides it for experiments).
-int digit_tile(int order, int vbytes) {
-  if (const char* e = getenv("QSD_TILE")) {
-    const int v = atoi(e);
-    if (v == 1024 || v == 2048 || v == 4096) return v;
-  }
+// Entries per tile: the requested size (4096, 2048 or 1024) if its two-slot
+// ring fits 227 KB of shared memory, else the largest that fits.
+int digit_tile(int order, int vbytes, int tile) {
   auto fits = [&](int T, size_t hdr) {
     const size_t rows = (size_t)order * (T * 4 + 16) + (vbytes ? (size_t)T * vbytes + 16 : 0);
     return hdr + 2 * rows <= 227 * 1024;
   };
-  if (fits(4096, ws_header<4096, 2, 16>())) return 4096;
-  if (fits(2048, ws_header<2048, 2, 16>())) return 2048;
+  const bool f4 = fits(4096, ws_header<4096, 2, 16>());
+  const bool f2 = fits(2048, ws_header<2048, 2, 16>());
+  if (tile == 4096 && f4) return 4096;
+  if ((tile == 2048 || tile == 4096) && f2) return 2048;
+  if (tile == 1024) return 1024;
+  if (f4) return 4096;
+  if (f2) return 2048;
   return 1024;
 }
 
-// Entries per chunk: 8 tiles (QSD_CHUNK_TILES overrides).
-int digit_chunk(int order, int vbytes) {
-  int k = 8;
-  if (const char* e = getenv("QSD_CHUNK_TILES")) {
-    const int v = atoi(e);
-    if (v >= 1 && v <= 256) k = v;
-  }
-  return k * digit_tile(order, vbytes);
+// Entries per chunk: chunk_tiles tiles (default 8, at most 256).
+int digit_chunk(int order, int vbytes, int tile, int chunk_tiles) {
+  const int k = chunk_tiles >= 1 && chunk_tiles <= 256 ? chunk_tiles : 8;
+  return k * digit_tile(order, vbytes, tile);
 }
 
 cudaError_t launch_chunk_hist(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
                               uint32_t* chunk_hist, uint32_t* group_sum, int* claim,
-                              int max_chunks, cudaStream_t stream) {
+                              int max_chunks, const PassBatch& pb, cudaStream_t stream) {
   int grid = sm_count() * 8;
   if (grid > max_chunks) grid = max_chunks;
   if (grid < 1) grid = 1;
-  k_chunk_hist<<<grid, kHistThreads, 0, stream>>>(c, ls, pd, chunk_hist, group_sum, claim);
+  PassTensor one;
+  one.c = c;
+  one.pd = pd;
+  k_chunk_hist<<<grid, kHistThreads, 0, stream>>>(one, ls, chunk_hist, group_sum, claim, pb);
   return cudaGetLastError();
 }
 
 cudaError_t launch_chunk_scan(const LargeSegs& ls, uint32_t* chunk_hist,
-                              const uint32_t* group_sum, int max_groups, cudaStream_t stream) {
+                              const uint32_t* group_sum, int max_groups, const PassBatch& pb,
+                              cudaStream_t stream) {
   int grid = sm_count() * 8;
   if (grid > max_groups) grid = max_groups;
   if (grid < 1) grid = 1;
-  k_chunk_scan<<<grid, kRadix, 0, stream>>>(ls, chunk_hist, group_sum);
+  k_chunk_scan<<<grid, kRadix, 0, stream>>>(ls, chunk_hist, group_sum, pb);
   return cudaGetLastError();
 }
 
 cudaError_t launch_digit_move(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
                               const uint32_t* chunk_off, int* claim, int max_chunks,
-                              unsigned* status, cudaStream_t stream) {
+                              unsigned* status, const PassBatch& pb, cudaStream_t stream) {
   switch (c.vbytes) {
-    case 0: return launch_move_vb<0>(c, ls, pd, chunk_off, claim, max_chunks, status, stream);
-    case 4: return launch_move_vb<4>(c, ls, pd, chunk_off, claim, max_chunks, status, stream);
-    case 8: return launch_move_vb<8>(c, ls, pd, chunk_off, claim, max_chunks, status, stream);
+    case 0: return launch_move_vb<0>(c, ls, pd, chunk_off, claim, max_chunks, status, pb, stream);
+    case 4: return launch_move_vb<4>(c, ls, pd, chunk_off, claim, max_chunks, status, pb, stream);
+    case 8: return launch_move_vb<8>(c, ls, pd, chunk_off, claim, max_chunks, status, pb, stream);
   }
   return cudaErrorInvalidValue;
 }

@@ -47,7 +47,7 @@ bool plan_has_prefix_group(const qsd_plan_s* p) {
 Layout layout_for(const qsd_plan_s* p, int64_t nnz, int vbytes) {
   Layout L;
   std::memset(&L, 0, sizeof(L));
-  const int CH = digit_chunk(p->order, vbytes);
+  const int CH = digit_chunk(p->order, vbytes, p->opts.tile, p->opts.chunk_tiles);
   const int C = p->local_capacity;
   int maxp = 0;
   for (int g = 0; g < p->ngroups; ++g) maxp = std::max(maxp, p->groups[g].npasses);
@@ -176,9 +176,17 @@ qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
     QSD_LAUNCH(tag("validate", -1, -1, nnz, 4 * plan->order),
                launch_validate(cur.c, cur.stride, plan->order, plan->dims, plan->tau, nnz,
                                status, st));
-  const int T = digit_tile(plan->order, has_vals ? vals->elem_bytes : 0);
-  const int CH = digit_chunk(plan->order, has_vals ? vals->elem_bytes : 0);
+  const int vb = has_vals ? vals->elem_bytes : 0;
+  const int T = digit_tile(plan->order, vb, plan->opts.tile);
+  const int CH = digit_chunk(plan->order, vb, plan->opts.tile, plan->opts.chunk_tiles);
   const int C = plan->local_capacity;
+  // one tensor: no batch tables
+  PassBatch pb1;
+  std::memset(&pb1, 0, sizeof(pb1));
+  LsBatch lb1;
+  std::memset(&lb1, 0, sizeof(lb1));
+  ClassifyBatch cb1;
+  std::memset(&cb1, 0, sizeof(cb1));
 
   for (int gi = 0; gi < plan->ngroups && nnz > 0; ++gi) {
     const Group& g = plan->groups[gi];
@@ -192,7 +200,8 @@ qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
     if (g.prefix_len == 0 && nnz <= C) {
       const int F = internal ? cur.idx ^ 1 : 0;
       QSD_LAUNCH(tag("local_sort", gi, -1, nnz, 2 * R),
-                 launch_local_sort(cols(cur, F), pl, nullptr, counters, 1, nnz, C, status, st));
+                 launch_local_sort(cols(cur, F), pl, nullptr, counters, 1, nnz, C, status, lb1,
+                                   st));
       cur = buf_src(F);
       continue;
     }
@@ -226,11 +235,11 @@ qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
       QSD_LAUNCH(tag("seg_classify", gi, -1, nnz, 0),
                  launch_seg_classify(seg_start, counters, nnz, C, CH, large, chunk_base,
                                      group_base, chunk_owner, group_owner, group_sum, P,
-                                     L.max_groups, st));
+                                     L.max_groups, cb1, st));
       // small buckets: straight into F (in place when F is the input buffer)
       QSD_LAUNCH(tag("local_sort", gi, -1, -1, 2 * R, 1),
                  launch_local_sort(cols(cur, F), pl, seg_start, counters, 0, nnz, C, status,
-                                   st));
+                                   lb1, st));
       ls.single = 0;
       ls.seg = large;
       ls.chunk_base = chunk_base;
@@ -253,12 +262,13 @@ qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
       }
       QSD_LAUNCH(tag("chunk_hist", gi, p, large_entries, 4 * nf),
                  launch_chunk_hist(cols(in, dst(p)), ls, g.pass[p], chunk_hist, gs,
-                                   counters + kCntClaim + 2 * p, max_chunks, st));
+                                   counters + kCntClaim + 2 * p, max_chunks, pb1, st));
       QSD_LAUNCH(tag("chunk_scan", gi, p, large_entries, 0),
-                 launch_chunk_scan(ls, chunk_hist, gs, max_groups, st));
+                 launch_chunk_scan(ls, chunk_hist, gs, max_groups, pb1, st));
       QSD_LAUNCH(tag("digit_move", gi, p, large_entries, 2 * R),
                  launch_digit_move(cols(in, dst(p)), ls, g.pass[p], chunk_hist,
-                                   counters + kCntClaim + 2 * p + 1, max_chunks, status, st));
+                                   counters + kCntClaim + 2 * p + 1, max_chunks, status, pb1,
+                                   st));
     }
     cur = buf_src(F);
   }

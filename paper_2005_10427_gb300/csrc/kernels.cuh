@@ -17,7 +17,9 @@ enum Counter {
   kCntNumGroups = 4,     // chunk groups over all large buckets
   kCntLargeEntries = 5,  // entries inside large buckets
   kCntClaim = 6,         // per pass: chunk claims of the histogram and move kernels
-  kNumCounters = 6 + 2 * kMaxPasses
+  kCntPassChunks = 6 + 2 * kMaxPasses,  // per pass (batches): active chunks
+  kCntPassGroups = 6 + 3 * kMaxPasses,  // per pass (batches): active chunk groups
+  kNumCounters = 6 + 4 * kMaxPasses
 };
 
 // Chunks per chunk group (the unit of the offset scan).
@@ -57,43 +59,116 @@ struct PassList {
   PassDesc pass[kMaxPasses];
 };
 
+// ---------------------------------------------------------------------------
+// Batches. One round of a batch runs the same group index of many tensors
+// together: they lie end to end in one index space, tensor k holding entries
+// [jbase[k], jbase[k+1]), and its buckets, chunks and output slots are
+// numbered in that space. A tensor's rows are reached through pointers
+// shifted back by jbase[k] elements, so entry J of the space is element J of
+// them and the kernels' index arithmetic is the single-tensor one.
+
+// Bucket discovery of a round: tensor k covers discovery tiles
+// [tile_base[k], tile_base[k+1]); its buckets are the runs of equal prefix
+// coordinates (a tensor with no prefix is one bucket).
+struct SegTensor {
+  const int32_t* col[kMaxOrder];  // shifted prefix rows
+  int n;                          // prefix length
+};
+struct SegBatch {
+  int n;                  // tensors; 0 = one tensor (the launch's own arguments)
+  const int* jbase;       // [n + 1]
+  const int* tile_base;   // [n + 1]
+  const SegTensor* t;     // [n]
+};
+
+// A tensor of a round as the shared-memory bucket sort sees it.
+struct LsTensor {
+  Cols c;                // shifted; input rows -> the rows its group ends in
+  int npasses;           // key passes of its group
+  const PassDesc* pass;  // [npasses], device memory
+};
+struct LsBatch {
+  int n;                 // 0 = one tensor
+  const int* jbase;      // [n + 1]
+  const LsTensor* t;     // [n]
+};
+
+// A tensor at one pass of a round: its buffers and the pass's digit.
+struct PassTensor {
+  Cols c;  // shifted
+  PassDesc pd;
+};
+
+// The work of one pass of a round: the chunks (and chunk groups) of the
+// tensors that have this pass, listed by the classification.
+struct PassBatch {
+  const PassTensor* t;      // [tensors]; null = one tensor
+  const int* large_tensor;  // tensor of each large bucket
+  const int* chunks;        // active chunk ids
+  const int* groups;        // active chunk-group ids
+  const int* counters;      // kCntPassChunks + pass / kCntPassGroups + pass
+  int pass;
+};
+
+// Where the classification records a round's per-pass work.
+struct ClassifyBatch {
+  int n;                  // 0 = one tensor
+  const int* jbase;       // [n + 1]
+  const LsTensor* t;      // [n] (for npasses)
+  int* large_tensor;      // [max_large]
+  int* pass_chunks;       // [max_passes][max_chunks]
+  int* pass_groups;       // [max_passes][max_groups]
+  int max_chunks;
+};
+
 // Launch helpers (return a CUDA error code; 0 on success).
 cudaError_t launch_seg_discover(const int32_t* const* prefix_cols, int nprefix,
                                 int nnz, int* seg_start, uint32_t* seg_lb,
                                 int* counters, unsigned* status,
                                 cudaStream_t stream);
+// The same over a batch round of `ntiles` discovery tiles and `nnz` entries.
+cudaError_t launch_seg_discover_batch(const SegBatch& sb, int ntiles, int nnz, int* seg_start,
+                                      uint32_t* seg_lb, int* counters, cudaStream_t stream);
+int seg_tile_entries();  // entries per discovery tile
 // Buckets larger than small_max are numbered and cut into chunks of `chunk`
 // entries and groups of kGroupChunks chunks; their group sums for every pass
 // (group_sum[pass][group][kRadix]) are zeroed.
 cudaError_t launch_seg_classify(const int* seg_start, int* counters, int nnz, int small_max,
                                 int chunk, int2* large, int* chunk_base, int* group_base,
                                 int* chunk_owner, int* group_owner, uint32_t* group_sum,
-                                int npasses, int max_groups, cudaStream_t stream);
+                                int npasses, int max_groups, const ClassifyBatch& cb,
+                                cudaStream_t stream);
 cudaError_t launch_validate(const int32_t* coords, int64_t stride, int order,
                             const int64_t* dims, const int* tau, int nnz,
                             unsigned* status, cudaStream_t stream);
 
 // Global digit passes (reduce, scan, move):
-int digit_tile(int order, int vbytes);   // entries per tile
-int digit_chunk(int order, int vbytes);  // entries per chunk
+// Entries per tile and per chunk; `tile` and `chunk_tiles` are requests
+// (0 = automatic), honoured when the tile fits shared memory.
+int digit_tile(int order, int vbytes, int tile = 0);
+int digit_chunk(int order, int vbytes, int tile = 0, int chunk_tiles = 0);
 // Per chunk: histogram of the pass's digit into chunk_hist[chunk][kRadix];
 // adds each chunk's counts into group_sum[group][kRadix] (zeroed before).
+// With a batch (pb.t set) `c` only gives the layout (largest order, value
+// width) and `pd` is unused: each chunk takes its tensor's buffers and digit.
 cudaError_t launch_chunk_hist(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
                               uint32_t* chunk_hist, uint32_t* group_sum, int* claim,
-                              int max_chunks, cudaStream_t stream);
+                              int max_chunks, const PassBatch& pb, cudaStream_t stream);
 // Per chunk group: turns chunk_hist into each chunk's first output slot per
 // digit (bucket start + digits below + the same digit in earlier chunks).
 cudaError_t launch_chunk_scan(const LargeSegs& ls, uint32_t* chunk_hist,
-                              const uint32_t* group_sum, int max_groups, cudaStream_t stream);
+                              const uint32_t* group_sum, int max_groups, const PassBatch& pb,
+                              cudaStream_t stream);
 // Moves every row of every chunk to its digit's slots, tile by tile.
 cudaError_t launch_digit_move(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
                               const uint32_t* chunk_off, int* claim, int max_chunks,
-                              unsigned* status, cudaStream_t stream);
+                              unsigned* status, const PassBatch& pb, cudaStream_t stream);
 
+// With a batch (lb.n > 0) `c` only gives the value width and `pl` is unused.
 cudaError_t launch_local_sort(const Cols& c, const PassList& pl,
                               const int* seg_start, const int* counters,
                               int single, int nnz, int capacity,
-                              unsigned* status, cudaStream_t stream);
+                              unsigned* status, const LsBatch& lb, cudaStream_t stream);
 
 // Copies every coordinate row and the values from c.in to c.out (entries
 // [0, nnz)): a zero-pass plan asked for a distinct output buffer.

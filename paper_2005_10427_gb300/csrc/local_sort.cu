@@ -11,7 +11,10 @@
 // stable ranking in shared memory. Only a permutation of batch positions is
 // sorted; each coordinate row and the values then move once: the row's batch
 // range is staged in shared memory and written back permuted with coalesced
-// stores, so the kernel may write its output over its input.
+// stores, so the kernel may write its output over its input. In a batch
+// round the buckets of several tensors share the index space; a batch of
+// buckets never crosses from one tensor into the next, and each takes its
+// tensor's rows and digits.
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -42,6 +45,9 @@ struct LsShared {
   uint16_t perm[2][CAP];
   uint16_t segid[CAP];
   int first, last, batch_end;
+  Cols c;                  // the current batch's tensor: rows
+  const PassDesc* passes;  // and key passes
+  int npasses;
 };
 
 // First index i in [lo, hi) with a[i] > x (or hi).
@@ -63,8 +69,8 @@ __device__ __forceinline__ int lower_bound_i(const int* a, int lo, int hi, int x
 
 template <int CAP, int VB>
 __global__ void __launch_bounds__(kLsThreads)
-k_local_sort(Cols c, PassList pl, const int* __restrict__ seg_start,
-             const int* __restrict__ counters, int single, int nnz) {
+k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict__ seg_start,
+             const int* __restrict__ counters, int single, int nnz, LsBatch lb) {
   constexpr int ITEMS = CAP / kLsThreads;
   extern __shared__ __align__(16) uint8_t smem[];
   LsShared<CAP>& S = *reinterpret_cast<LsShared<CAP>*>(smem);
@@ -76,6 +82,9 @@ k_local_sort(Cols c, PassList pl, const int* __restrict__ seg_start,
   const int nseg = single ? 1 : counters[kCntNumSeg];
 
   if (threadIdx.x == 0) {
+    S.c = c1;
+    S.passes = pl.pass;
+    S.npasses = pl.npasses;
     if (single) {
       S.first = 0;
       S.last = 1;
@@ -92,13 +101,22 @@ k_local_sort(Cols c, PassList pl, const int* __restrict__ seg_start,
       const int a = single ? 0 : seg_start[s];
       const int b = single ? nnz : seg_start[s + 1];
       int e;
+      int lim = last;
+      if (lb.n > 0) {  // the bucket's tensor; the batch ends where the next one starts
+        const int k = upper_bound_i(lb.jbase, 0, lb.n + 1, a) - 1;
+        S.c = lb.t[k].c;
+        S.passes = lb.t[k].pass;
+        S.npasses = lb.t[k].npasses;
+        const int tb = lower_bound_i(seg_start, s + 1, nseg + 1, lb.jbase[k + 1]);
+        if (tb < lim) lim = tb;
+      }
       if (b - a > CAP) {
         e = -1;  // large bucket: sorted by the digit passes
       } else if (single) {
         e = 1;
       } else {
         e = upper_bound_i(seg_start, s + 1, nseg + 1, a + CAP) - 1;
-        if (e > last) e = last;
+        if (e > lim) e = lim;
       }
       S.batch_end = e;
     }
@@ -109,6 +127,9 @@ k_local_sort(Cols c, PassList pl, const int* __restrict__ seg_start,
       ++s;
       continue;
     }
+    const Cols& c = S.c;
+    const int key_passes = S.npasses;
+    const PassDesc* const passes = S.passes;
     const int A = single ? 0 : seg_start[s];
     const int n = (single ? nnz : seg_start[e]) - A;
     const int nsb = e - s;
@@ -140,7 +161,6 @@ k_local_sort(Cols c, PassList pl, const int* __restrict__ seg_start,
     int cur = 0;
     int seg_bits = 0;
     while ((1 << seg_bits) < nsb) ++seg_bits;
-    const int key_passes = pl.npasses;
     const int seg_passes = (seg_bits + kRadixBits - 1) / kRadixBits;
     for (int p = 0; p < key_passes + seg_passes; ++p) {
       uint32_t dig[ITEMS], rank[ITEMS], el[ITEMS];
@@ -151,7 +171,7 @@ k_local_sort(Cols c, PassList pl, const int* __restrict__ seg_start,
         uint32_t d = kRadix - 1;
         if (pos < n) {
           if (p < key_passes) {
-            const PassDesc& pd = pl.pass[p];
+            const PassDesc& pd = passes[p];
             d = 0;
             for (int k = 0; k < pd.nfields; ++k) {
               const DigitField f = pd.f[k];
@@ -196,7 +216,8 @@ k_local_sort(Cols c, PassList pl, const int* __restrict__ seg_start,
 
 template <int CAP, int VB>
 cudaError_t launch_ls(const Cols& c, const PassList& pl, const int* seg_start,
-                      const int* counters, int single, int nnz, cudaStream_t stream) {
+                      const int* counters, int single, int nnz, const LsBatch& lb,
+                      cudaStream_t stream) {
   const size_t smem = ((sizeof(LsShared<CAP>) + 15) & ~size_t(15)) +
                       (size_t)CAP * (VB == 8 ? 8 : 4);
   cudaError_t e = cudaFuncSetAttribute(k_local_sort<CAP, VB>,
@@ -206,17 +227,18 @@ cudaError_t launch_ls(const Cols& c, const PassList& pl, const int* seg_start,
   const int grid = single ? 1 : (nnz + CAP - 1) / CAP;
   if (grid < 1) return cudaSuccess;
   k_local_sort<CAP, VB><<<grid, kLsThreads, smem, stream>>>(c, pl, seg_start, counters,
-                                                            single, nnz);
+                                                            single, nnz, lb);
   return cudaGetLastError();
 }
 
 template <int CAP>
 cudaError_t launch_ls_cap(const Cols& c, const PassList& pl, const int* seg_start,
-                          const int* counters, int single, int nnz, cudaStream_t stream) {
+                          const int* counters, int single, int nnz, const LsBatch& lb,
+                          cudaStream_t stream) {
   switch (c.vbytes) {
-    case 0: return launch_ls<CAP, 0>(c, pl, seg_start, counters, single, nnz, stream);
-    case 4: return launch_ls<CAP, 4>(c, pl, seg_start, counters, single, nnz, stream);
-    case 8: return launch_ls<CAP, 8>(c, pl, seg_start, counters, single, nnz, stream);
+    case 0: return launch_ls<CAP, 0>(c, pl, seg_start, counters, single, nnz, lb, stream);
+    case 4: return launch_ls<CAP, 4>(c, pl, seg_start, counters, single, nnz, lb, stream);
+    case 8: return launch_ls<CAP, 8>(c, pl, seg_start, counters, single, nnz, lb, stream);
   }
   return cudaErrorInvalidValue;
 }
@@ -225,13 +247,13 @@ cudaError_t launch_ls_cap(const Cols& c, const PassList& pl, const int* seg_star
 
 cudaError_t launch_local_sort(const Cols& c, const PassList& pl, const int* seg_start,
                               const int* counters, int single, int nnz, int capacity,
-                              unsigned* status, cudaStream_t stream) {
+                              unsigned* status, const LsBatch& lb, cudaStream_t stream) {
   (void)status;
   switch (capacity) {
-    case 1024: return launch_ls_cap<1024>(c, pl, seg_start, counters, single, nnz, stream);
-    case 2048: return launch_ls_cap<2048>(c, pl, seg_start, counters, single, nnz, stream);
-    case 4096: return launch_ls_cap<4096>(c, pl, seg_start, counters, single, nnz, stream);
-    case 8192: return launch_ls_cap<8192>(c, pl, seg_start, counters, single, nnz, stream);
+    case 1024: return launch_ls_cap<1024>(c, pl, seg_start, counters, single, nnz, lb, stream);
+    case 2048: return launch_ls_cap<2048>(c, pl, seg_start, counters, single, nnz, lb, stream);
+    case 4096: return launch_ls_cap<4096>(c, pl, seg_start, counters, single, nnz, lb, stream);
+    case 8192: return launch_ls_cap<8192>(c, pl, seg_start, counters, single, nnz, lb, stream);
   }
   return cudaErrorInvalidValue;
 }

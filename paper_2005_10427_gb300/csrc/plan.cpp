@@ -96,6 +96,9 @@ qsd_status qsd_plan_ex(int order, const int64_t* dims,
       o.local_capacity != 2048 && o.local_capacity != 4096 &&
       o.local_capacity != 8192)
     return QSD_ERR_INVALID_ARGUMENT;
+  if (o.tile != 0 && o.tile != 1024 && o.tile != 2048 && o.tile != 4096)
+    return QSD_ERR_INVALID_ARGUMENT;
+  if (o.chunk_tiles < 0 || o.chunk_tiles > 256) return QSD_ERR_INVALID_ARGUMENT;
 
   qsd_plan_s* p = new (std::nothrow) qsd_plan_s;
   if (!p) return QSD_ERR_OUT_OF_MEMORY;

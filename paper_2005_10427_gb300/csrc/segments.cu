@@ -24,46 +24,94 @@ struct PrefixCols {
 
 // Bucket starts in three steps with no dependency between blocks:
 //   k_seg_count  per tile of kSegTile entries: flag[j] = 1 when j starts a
-//                bucket (j == 0, or a prefix coordinate differs from entry
-//                j-1); the flags are kept as one bit per entry (the warp
-//                ballots) and the tile's count is stored;
+//                bucket (j is the tensor's first entry, or a prefix
+//                coordinate differs from entry j-1); the flags are kept as
+//                one bit per entry (the warp ballots) and the tile's count is
+//                stored;
 //   k_seg_scan   one block: exclusive prefix of the tile counts, the bucket
 //                count, and the sentinel seg_start[nseg] = nnz;
 //   k_seg_write  per tile: the flagged positions, compacted in order into
 //                seg_start.
 // Each warp covers kSegItems consecutive 32-entry pieces, so the ballot of
-// round i of warp w holds entries [32 * word, 32 * word + 32) where
-// word = tile * kSegTile / 32 + w * kSegItems + i.
+// round i of warp w holds entries [j0 + 32 * (w * kSegItems + i), +32) of the
+// tile starting at entry j0, stored at word tile * kSegTile / 32 +
+// w * kSegItems + i. A batch round gives each tensor its own tiles.
+
+// The entries [j0, j1) of discovery tile t and the tensor's first entry.
+struct SegTileSpan {
+  int j0, j1, first, k;
+};
+
+__device__ __forceinline__ int upper_bound_int(const int* a, int lo, int hi, int x) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ SegTileSpan seg_tile_span(const SegBatch& sb, int nnz, int t) {
+  SegTileSpan sp;
+  if (sb.n == 0) {
+    sp.k = 0;
+    sp.first = 0;
+    sp.j0 = t * kSegTile;
+    sp.j1 = nnz;
+  } else {
+    sp.k = upper_bound_int(sb.tile_base, 0, sb.n + 1, t) - 1;
+    sp.first = __ldg(sb.jbase + sp.k);
+    sp.j0 = sp.first + (t - __ldg(sb.tile_base + sp.k)) * kSegTile;
+    sp.j1 = __ldg(sb.jbase + sp.k + 1);
+  }
+  if (sp.j1 > sp.j0 + kSegTile) sp.j1 = sp.j0 + kSegTile;
+  return sp;
+}
+
 __global__ void __launch_bounds__(kSegThreads)
-k_seg_count(PrefixCols pc, int nnz, uint32_t* __restrict__ bits,
+k_seg_count(PrefixCols pc1, SegBatch sb, int nnz, uint32_t* __restrict__ bits,
             uint32_t* __restrict__ tile_count) {
   __shared__ uint32_t s_warp[kSegWarps];
+  __shared__ const int32_t* s_col[kMaxOrder];
+  __shared__ int s_n;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int t = blockIdx.x;
-  const int base = t * kSegTile + w * kSegItems * 32;
+  const SegTileSpan sp = seg_tile_span(sb, nnz, t);
+  if (threadIdx.x < kMaxOrder) {
+    if (sb.n == 0) {
+      s_col[threadIdx.x] = pc1.col[threadIdx.x];
+      if (threadIdx.x == 0) s_n = pc1.n;
+    } else {
+      s_col[threadIdx.x] = sb.t[sp.k].col[threadIdx.x];
+      if (threadIdx.x == 0) s_n = sb.t[sp.k].n;
+    }
+  }
+  __syncthreads();
+  const int np = s_n;
+  const int base = sp.j0 + w * kSegItems * 32;
+  const int wbase = t * (kSegTile / 32) + w * kSegItems;
   uint32_t cnt = 0;
   int32_t prev[kMaxOrder];
   // the entry before this warp's first one
-  for (int m = 0; m < pc.n; ++m) {
+  for (int m = 0; m < np; ++m) {
     const int jp = base + lane - 1;
-    prev[m] = (lane == 0 && jp >= 0 && jp < nnz) ? __ldg(pc.col[m] + jp) : 0;
+    prev[m] = (lane == 0 && jp >= sp.first && jp < sp.j1) ? __ldg(s_col[m] + jp) : 0;
   }
 #pragma unroll 4
   for (int i = 0; i < kSegItems; ++i) {
     const int j = base + i * 32 + lane;
-    const bool in = j < nnz;
-    bool flag = in && j == 0;
-    for (int m = 0; m < pc.n; ++m) {
-      const int32_t v = in ? __ldg(pc.col[m] + j) : 0;
+    const bool in = j < sp.j1;
+    bool flag = in && j == sp.first;
+    for (int m = 0; m < np; ++m) {
+      const int32_t v = in ? __ldg(s_col[m] + j) : 0;
       // entry j-1: lane-1's value, or for lane 0 the previous round's last lane
       int32_t p = __shfl_up_sync(0xffffffffu, v, 1);
       const int32_t last = __shfl_sync(0xffffffffu, v, 31);
       if (lane == 0) p = prev[m];
       prev[m] = last;
-      flag |= in && j > 0 && v != p;
+      flag |= in && j > sp.first && v != p;
     }
     const uint32_t bal = __ballot_sync(0xffffffffu, flag);
-    if (lane == 0 && (base + i * 32) < nnz) bits[(base >> 5) + i] = bal;
+    if (lane == 0 && (base + i * 32) < sp.j1) bits[wbase + i] = bal;
     cnt += __popc(bal);
   }
   if (lane == 0) s_warp[w] = cnt;
@@ -100,16 +148,18 @@ k_seg_scan(uint32_t* __restrict__ tile_count, int ntiles, int nnz, int* __restri
 }
 
 __global__ void __launch_bounds__(kSegThreads)
-k_seg_write(int nnz, const uint32_t* __restrict__ bits, const uint32_t* __restrict__ tile_off,
-            int* __restrict__ seg_start) {
+k_seg_write(SegBatch sb, int nnz, const uint32_t* __restrict__ bits,
+            const uint32_t* __restrict__ tile_off, int* __restrict__ seg_start) {
   __shared__ uint32_t s_tmp[kSegWarps + 1];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int t = blockIdx.x;
-  const int base = t * kSegTile + w * kSegItems * 32;
+  const SegTileSpan sp = seg_tile_span(sb, nnz, t);
+  const int base = sp.j0 + w * kSegItems * 32;
+  const int wbase = t * (kSegTile / 32) + w * kSegItems;
   uint32_t bal[kSegItems], cnt = 0;
 #pragma unroll
   for (int i = 0; i < kSegItems; ++i) {
-    bal[i] = (base + i * 32) < nnz ? bits[(base >> 5) + i] : 0u;
+    bal[i] = (base + i * 32) < sp.j1 ? bits[wbase + i] : 0u;
     cnt += __popc(bal[i]);
   }
   uint32_t total;
@@ -126,12 +176,15 @@ k_seg_write(int nnz, const uint32_t* __restrict__ bits, const uint32_t* __restri
 
 // Buckets larger than small_max go to the digit passes: each gets an index,
 // a contiguous range of chunk ids and of chunk-group ids (so a bucket's
-// chunks are consecutive), and zeroed group sums for every pass.
+// chunks are consecutive), and zeroed group sums for each of its passes. In
+// a batch round the bucket's tensor is recorded, and its chunks and groups
+// are listed for every pass that tensor has (tensors differ in passes).
 __global__ void k_seg_classify(const int* __restrict__ seg_start, int* __restrict__ counters,
                                int small_max, int chunk, int2* __restrict__ large,
                                int* __restrict__ chunk_base, int* __restrict__ group_base,
                                int* __restrict__ chunk_owner, int* __restrict__ group_owner,
-                               uint32_t* __restrict__ group_sum, int npasses, int max_groups) {
+                               uint32_t* __restrict__ group_sum, int npasses, int max_groups,
+                               ClassifyBatch cb) {
   const int nseg = counters[kCntNumSeg];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nseg; i += gridDim.x * blockDim.x) {
     const int a = seg_start[i], b = seg_start[i + 1];
@@ -139,17 +192,29 @@ __global__ void k_seg_classify(const int* __restrict__ seg_start, int* __restric
     const int idx = atomicAdd(&counters[kCntNumLarge], 1);
     const int nc = (b - a + chunk - 1) / chunk;
     const int ng = (nc + kGroupChunks - 1) / kGroupChunks;
-    const int cb = atomicAdd(&counters[kCntNumChunks], nc);
-    const int gb = atomicAdd(&counters[kCntNumGroups], ng);
+    const int cbase = atomicAdd(&counters[kCntNumChunks], nc);
+    const int gbase = atomicAdd(&counters[kCntNumGroups], ng);
     atomicAdd(&counters[kCntLargeEntries], b - a);
     large[idx] = make_int2(a, b);
-    chunk_base[idx] = cb;
-    group_base[idx] = gb;
-    for (int j = 0; j < nc; ++j) chunk_owner[cb + j] = idx;
+    chunk_base[idx] = cbase;
+    group_base[idx] = gbase;
+    int np = npasses;
+    if (cb.n > 0) {
+      const int k = upper_bound_int(cb.jbase, 0, cb.n + 1, a) - 1;
+      cb.large_tensor[idx] = k;
+      np = cb.t[k].npasses;
+      for (int p = 0; p < np; ++p) {
+        const int lc = atomicAdd(&counters[kCntPassChunks + p], nc);
+        for (int j = 0; j < nc; ++j) cb.pass_chunks[(size_t)p * cb.max_chunks + lc + j] = cbase + j;
+        const int lg = atomicAdd(&counters[kCntPassGroups + p], ng);
+        for (int j = 0; j < ng; ++j) cb.pass_groups[(size_t)p * max_groups + lg + j] = gbase + j;
+      }
+    }
+    for (int j = 0; j < nc; ++j) chunk_owner[cbase + j] = idx;
     for (int j = 0; j < ng; ++j) {
-      group_owner[gb + j] = idx;
-      for (int p = 0; p < npasses; ++p) {
-        uint4* row = reinterpret_cast<uint4*>(group_sum + ((size_t)p * max_groups + gb + j) * kRadix);
+      group_owner[gbase + j] = idx;
+      for (int p = 0; p < np; ++p) {
+        uint4* row = reinterpret_cast<uint4*>(group_sum + ((size_t)p * max_groups + gbase + j) * kRadix);
         for (int k = 0; k < kRadix / 4; ++k) row[k] = make_uint4(0, 0, 0, 0);
       }
     }
@@ -203,24 +268,49 @@ cudaError_t launch_seg_discover(const int32_t* const* prefix_cols, int nprefix,
   for (int m = 0; m < kMaxOrder; ++m) pc.col[m] = m < nprefix ? prefix_cols[m] : nullptr;
   const int ntiles = (nnz + kSegTile - 1) / kSegTile;
   if (ntiles == 0) return cudaSuccess;
+  SegBatch sb;
+  sb.n = 0;
+  sb.jbase = nullptr;
+  sb.tile_base = nullptr;
+  sb.t = nullptr;
   // seg_lb holds the tile counts (ntiles words) followed by the flag bits
   uint32_t* tile_count = seg_lb;
   uint32_t* bits = seg_lb + ntiles + 1;
-  k_seg_count<<<ntiles, kSegThreads, 0, stream>>>(pc, nnz, bits, tile_count);
+  k_seg_count<<<ntiles, kSegThreads, 0, stream>>>(pc, sb, nnz, bits, tile_count);
   k_seg_scan<<<1, 1024, 0, stream>>>(tile_count, ntiles, nnz, seg_start, counters);
-  k_seg_write<<<ntiles, kSegThreads, 0, stream>>>(nnz, bits, tile_count, seg_start);
+  k_seg_write<<<ntiles, kSegThreads, 0, stream>>>(sb, nnz, bits, tile_count, seg_start);
   return cudaGetLastError();
 }
 
-// Words of scratch for bucket discovery: tile counts, then one bit per entry.
+cudaError_t launch_seg_discover_batch(const SegBatch& sb, int ntiles, int nnz, int* seg_start,
+                                      uint32_t* seg_lb, int* counters, cudaStream_t stream) {
+  if (ntiles == 0) return cudaSuccess;
+  PrefixCols pc;
+  pc.n = 0;
+  for (int m = 0; m < kMaxOrder; ++m) pc.col[m] = nullptr;
+  uint32_t* tile_count = seg_lb;
+  uint32_t* bits = seg_lb + ntiles + 1;
+  k_seg_count<<<ntiles, kSegThreads, 0, stream>>>(pc, sb, nnz, bits, tile_count);
+  k_seg_scan<<<1, 1024, 0, stream>>>(tile_count, ntiles, nnz, seg_start, counters);
+  k_seg_write<<<ntiles, kSegThreads, 0, stream>>>(sb, nnz, bits, tile_count, seg_start);
+  return cudaGetLastError();
+}
+
+int seg_tile_entries() { return kSegTile; }
+
+// Words of scratch for bucket discovery over nnz entries in one tensor:
+// tile counts, then one bit per entry. (A batch round sizes it by its tile
+// count: ntiles + 1 + ntiles * kSegTile / 32 + kSegItems.)
 int seg_lookback_words(int nnz) {
-  return (nnz + kSegTile - 1) / kSegTile + 1 + (nnz + 31) / 32 + kSegItems;
+  const int ntiles = (nnz + kSegTile - 1) / kSegTile;
+  return ntiles + 1 + ntiles * (kSegTile / 32) + kSegItems;
 }
 
 cudaError_t launch_seg_classify(const int* seg_start, int* counters, int nnz, int small_max,
                                 int chunk, int2* large, int* chunk_base, int* group_base,
                                 int* chunk_owner, int* group_owner, uint32_t* group_sum,
-                                int npasses, int max_groups, cudaStream_t stream) {
+                                int npasses, int max_groups, const ClassifyBatch& cb,
+                                cudaStream_t stream) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -229,7 +319,7 @@ cudaError_t launch_seg_classify(const int* seg_start, int* counters, int nnz, in
   if (blocks < 1) blocks = 1;
   k_seg_classify<<<blocks, 256, 0, stream>>>(seg_start, counters, small_max, chunk, large,
                                              chunk_base, group_base, chunk_owner, group_owner,
-                                             group_sum, npasses, max_groups);
+                                             group_sum, npasses, max_groups, cb);
   return cudaGetLastError();
 }
 

@@ -258,3 +258,46 @@ def batch_workload(n_tensors: int = 256, seed: int = 4, nnz_lo: float = 1e3,
                         dists=[("zipf", zipf)] * r, val_kind="f32_normal",
                         seed=seed * 100003 + i, perm=perm))
     return out
+
+
+def serving_workload(n_tensors: int = 64, n_requests: int = 10_000, rate: float = 2000.0,
+                     seed: int = 5, nnz_lo: float = 1e4, nnz_hi: float = 5e7,
+                     dim_lo: float = 100, dim_hi: float = 1e6, zipf: float = 1.2):
+    """The serving workload: a resident pool and a Poisson request stream.
+
+    Pool: n_tensors tensors, order uniform in {3,4}, nnz log-uniform in
+    [nnz_lo, nnz_hi], each dim log-uniform in [dim_lo, dim_hi] (redrawn until
+    prod(dims) >= 8 * nnz), Zipf(zipf) coordinates, float64 N(0,1) values,
+    identity input order. Requests: exponential inter-arrival times at `rate`
+    per second; each picks a pool tensor uniformly and a uniformly random
+    non-identity target order. Returns (pool descriptions, [(arrival offset
+    in seconds, tensor index, target order)]).
+    """
+    g = torch.Generator()
+    g.manual_seed(seed)
+    pool = []
+    for i in range(n_tensors):
+        r = int(torch.randint(3, 5, (1,), generator=g))
+        u = float(torch.rand(1, generator=g, dtype=torch.float64))
+        nnz = int(round(math.exp(math.log(nnz_lo) + u * (math.log(nnz_hi) - math.log(nnz_lo)))))
+        while True:
+            us = torch.rand(r, generator=g, dtype=torch.float64)
+            dims = [int(round(math.exp(math.log(dim_lo) + float(x) * (math.log(dim_hi) -
+                                                                       math.log(dim_lo)))))
+                    for x in us]
+            if math.prod(dims) >= 8 * nnz:
+                break
+        pool.append(dict(name=f"serve{i}", dims=dims, nnz=nnz, dists=[("zipf", zipf)] * r,
+                         val_kind="f64_normal", seed=seed * 100003 + i))
+    gaps = -torch.log1p(-torch.rand(n_requests, generator=g, dtype=torch.float64)) / rate
+    times = torch.cumsum(gaps, 0)
+    reqs = []
+    for k in range(n_requests):
+        i = int(torch.randint(0, n_tensors, (1,), generator=g))
+        r = len(pool[i]["dims"])
+        while True:
+            perm = tuple(int(x) for x in torch.randperm(r, generator=g))
+            if perm != tuple(range(r)):
+                break
+        reqs.append((float(times[k]), i, perm))
+    return pool, reqs
