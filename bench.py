@@ -130,26 +130,29 @@ def committed_traffic(kernel: str, workload: str):
 
 
 def cpu_oracle_rate(t_coords: np.ndarray, t_vals: np.ndarray, perms, target_s=15.0):
-    """The oracle (single-threaded std::stable_sort) on a prefix sample."""
+    """The oracle (single-threaded std::stable_sort) on a strided sample of the
+    workload (every k-th entry: still sorted in the input order, with the
+    workload's distribution), sized to about target_s seconds."""
     import oracle
     n_total = t_coords.shape[1]
-    m = min(n_total, 500_000)
-    t0 = time.perf_counter()
-    for sigma in perms:
-        oracle.transpose(t_coords[:, :m], t_vals[:m], sigma)
-    dt = time.perf_counter() - t0
-    # grow the sample towards target_s seconds of work (n log n: aim a bit low)
-    scale = max(1.0, 0.7 * target_s / max(dt, 1e-3))
-    m2 = int(min(n_total, m * scale))
-    if m2 > m:
-        m = m2
+
+    def run(m):
+        idx = np.linspace(0, n_total - 1, m).astype(np.int64)
+        c, v = np.ascontiguousarray(t_coords[:, idx]), np.ascontiguousarray(t_vals[idx])
         t0 = time.perf_counter()
         for sigma in perms:
-            oracle.transpose(t_coords[:, :m], t_vals[:m], sigma)
-        dt = time.perf_counter() - t0
+            oracle.transpose(c, v, sigma)
+        return time.perf_counter() - t0
+
+    m = min(n_total, 400_000)
+    dt = run(m)
+    while m < n_total and dt < 0.4 * target_s:  # grow at most 4x per step (n log n)
+        m = int(min(n_total, m * min(4.0, 0.8 * target_s / max(dt, 1e-3))))
+        dt = run(m)
     return {"value": len(perms) * m / dt / 1e9, "unit": "Gnnz/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {m} entries of the workload (a sorted prefix), all "
-                      f"{len(perms)} target orders, std::stable_sort on 1 host core, {dt:.1f} s"}
+            "sample": f"{m} entries (every {n_total / m:.1f}-th of the workload, in input "
+                      f"order), all {len(perms)} target orders, std::stable_sort on 1 host "
+                      f"core, {dt:.1f} s"}
 
 
 def run_reference(args, rank, world):
@@ -204,6 +207,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 256-tensor batched-vs-single-calls measurement")
     ap.add_argument("--no-tune", action="store_true", help="batched run without autotuning")
+    ap.add_argument("--batched-steps", type=int, default=0,
+                    help="timed runs of the batched workload (default: steps, 5..20)")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the Poisson-stream serving measurement")
     args = ap.parse_args()
@@ -256,11 +261,13 @@ def main():
     time.sleep(0.3)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("single_timed")  # ncu --nvtx-include single_timed/
     ev0.record(stream)
     for _ in range(args.steps):
         step()
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
     if world > 1:
@@ -329,7 +336,7 @@ def main():
     batched = None
     if not args.no_batched:
         del cb, vbuf
-        batched = bench_batched(qsd, dev, stream, steps=max(5, min(args.steps, 20)),
+        batched = bench_batched(qsd, dev, stream, steps=args.batched_steps or max(5, min(args.steps, 20)),
                                 warmup=args.warmup, tune=not args.no_tune)
         cb = [torch.empty((r, nnz), dtype=torch.int32, device=dev) for _ in range(2)]
         vbuf = [torch.empty(nnz, dtype=t.vals.dtype, device=dev) for _ in range(2)]
@@ -408,11 +415,13 @@ def bench_batched(qsd, dev, stream, steps: int, warmup: int, tune: bool = True):
     for _ in range(warmup):
         batch.run(ws, stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("batched_timed")  # ncu --nvtx-include batched_timed/
     ev0.record(stream)
     for _ in range(steps):
         batch.run(ws, stream)
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     ms_b = ev0.elapsed_time(ev1) / steps
     if qsd.workspace_status(ws, stream) != 0:
         raise SystemExit("device status set by the batched run")
