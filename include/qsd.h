@@ -91,8 +91,8 @@ typedef struct {
                             radix sort over every mode (the baseline of
                             Section 3 that the method improves on) */
   int tile;              /* entries a global pass stages in shared memory at
-                            once: 1024, 2048 or 4096 (smaller when the rows
-                            do not fit); 0 = automatic */
+                            once: 1024, 2048, 3584 or 4096 (smaller when the
+                            rows do not fit); 0 = automatic */
   int chunk_tiles;       /* tiles per chunk, the unit of the per-chunk digit
                             counts, 1..256; 0 = automatic (8) */
 } qsd_plan_options;

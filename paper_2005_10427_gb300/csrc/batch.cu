@@ -475,7 +475,7 @@ bool valid_options(const qsd_batch_options& o) {
   if (o.local_capacity != 0 && o.local_capacity != 1024 && o.local_capacity != 2048 &&
       o.local_capacity != 4096 && o.local_capacity != 8192)
     return false;
-  if (o.tile != 0 && o.tile != 1024 && o.tile != 2048 && o.tile != 4096) return false;
+  if (o.tile != 0 && o.tile != 1024 && o.tile != 2048 && o.tile != 3584 && o.tile != 4096) return false;
   if (o.chunk_tiles < 0 || o.chunk_tiles > 256) return false;
   return true;
 }
@@ -646,13 +646,13 @@ qsd_status qsd_batch_tune(qsd_batch_t b, void* workspace, size_t workspace_bytes
   float best_ms = -1.f;
   qsd_status s = measure(best, &best_ms);
   // coordinate search: one option at a time, keeping the fastest
-  const int tiles[] = {4096, 2048, 1024};
+  const int tiles[] = {4096, 3584, 2048, 1024};
   const int bits[] = {8, 7, 6};
   const int caps[] = {4096, 2048, 8192};
   const int chunks[] = {8, 4, 16, 32};
   for (int dim = 0; dim < 4 && s == QSD_OK; ++dim) {
     const int* vals = dim == 0 ? tiles : dim == 1 ? bits : dim == 2 ? caps : chunks;
-    const int nv = dim == 3 ? 4 : 3;
+    const int nv = dim == 0 || dim == 3 ? 4 : 3;
     for (int k = 0; k < nv && s == QSD_OK; ++k) {
       qsd_batch_options o = best;
       int& field = dim == 0 ? o.tile

@@ -187,14 +187,24 @@ __device__ __forceinline__ bool group_all(bool pred) {
 // named barrier BAR only (other warps of the block may be doing other work).
 // Returns whether `ok` held on every ranking thread (reduced at the ranking's
 // first barrier, so a group can agree to stop at no extra cost).
+//
+// After the per-warp counts, one block-wide exclusive scan over the counters
+// taken digit-major (digit d's counters of warps 0..NWARPS-1, then digit d+1's)
+// gives every (digit, warp) pair its first sorted position: thread t reads the
+// counters of digit t / TPD for 8 consecutive warps (TPD = NWARPS / 8 threads
+// per digit), so the scan is 8 independent loads per thread and one scan of
+// one value per thread.
 template <int NWARPS, int ITEMS, int BAR = 0>
 __device__ __forceinline__ bool block_rank(const uint32_t (&dig)[ITEMS],
                                            uint32_t (&rank)[ITEMS],
                                            uint16_t* s_warp_hist,  // [NWARPS][kRadix]
                                            uint32_t* s_bin_start,  // [kRadix]
                                            uint32_t* s_bin_count,  // [kRadix]
+                                           uint32_t* s_tmp,        // [NWARPS]
                                            bool ok = true)
 {
+  static_assert(NWARPS % 8 == 0, "8 warps per scanning thread: NWARPS * 32 == kRadix * TPD");
+  constexpr int TPD = NWARPS / 8;  // scanning threads per digit
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   uint16_t* h = s_warp_hist + w * kRadix;
@@ -228,45 +238,42 @@ __device__ __forceinline__ bool block_rank(const uint32_t (&dig)[ITEMS],
     all_ok = __syncthreads_and(ok) != 0;
   else
     all_ok = group_all<BAR, NWARPS * 32>(ok);
-  // exclusive scan over warps for each digit; digit totals
-  for (int d = threadIdx.x; d < kRadix; d += NWARPS * 32) {
-    uint32_t run = 0;
+  // digit-major scan: thread t owns digit d = t / TPD, warps w0 .. w0 + 7
+  const int d = threadIdx.x / TPD, w0 = (threadIdx.x % TPD) * 8;
+  uint32_t c[8], local = 0;
 #pragma unroll
-    for (int ww = 0; ww < NWARPS; ++ww) {
-      uint32_t t = s_warp_hist[ww * kRadix + d];
-      s_warp_hist[ww * kRadix + d] = run;
-      run += t;
-    }
-    s_bin_count[d] = run;
+  for (int k = 0; k < 8; ++k) c[k] = s_warp_hist[(w0 + k) * kRadix + d];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const uint32_t x = c[k];
+    c[k] = local;  // exclusive within the thread's 8 warps
+    local += x;
   }
+  uint32_t incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_tmp[w] = incl;
   group_sync<BAR, NWARPS * 32>();
-  // exclusive scan over digits (one warp, kRadix/32 digits per lane)
-  if (w == 0) {
-    constexpr int PER = kRadix / 32;
-    uint32_t v[PER];
-    uint32_t sum = 0;
+  uint32_t wt = lane < NWARPS ? s_tmp[lane] : 0u;
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-      v[j] = s_bin_count[lane * PER + j];
-      sum += v[j];
-    }
-    uint32_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    uint32_t run = incl - sum;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-      s_bin_start[lane * PER + j] = run;
-      run += v[j];
-    }
+  for (int o = 1; o < NWARPS; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, wt, o);
+    if (lane >= o) wt += y;
   }
+  const uint32_t woff = w ? __shfl_sync(0xffffffffu, wt, w - 1) : 0u;
+  const uint32_t prefix = woff + incl - local;  // sorted positions before this thread's counters
+  const uint32_t dstart = __shfl_up_sync(0xffffffffu, prefix, threadIdx.x % TPD);
+  const int part = threadIdx.x % TPD;
+  if (part == 0) s_bin_start[d] = prefix;
+  if (part == TPD - 1) s_bin_count[d] = prefix + local - (TPD > 1 ? dstart : prefix);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s_warp_hist[(w0 + k) * kRadix + d] = (uint16_t)(prefix + c[k]);
   group_sync<BAR, NWARPS * 32>();
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i)
-    rank[i] += s_bin_start[dig[i]] + h[dig[i]];
+  for (int i = 0; i < ITEMS; ++i) rank[i] += h[dig[i]];
   return all_ok;
 }
 

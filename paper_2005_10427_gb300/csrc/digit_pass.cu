@@ -303,13 +303,15 @@ struct TileSlot {
 
 template <int T, int NS, int RW>
 struct WsShared {
-  uint64_t full[NS];     // producer -> rankers: tile staged
+  uint64_t kfull[NS];    // producer -> rankers: the tile's key rows staged
+  uint64_t full[NS];     // producer -> writers: the tile's other rows staged
   uint64_t empty[NS];    // writers -> producer: staging buffer free
   uint64_t ranked[2];    // rankers -> writers: destinations ready
   uint64_t consumed[2];  // writers -> rankers: destinations used
   TileSlot slot[NS];
   uint32_t off[kRadix];  // rankers: running output slot per digit of the chunk
   uint16_t warp_hist[RW * kRadix];
+  uint32_t rank_tmp[RW];  // block_rank's scan scratch
   uint32_t bin_start[kRadix];
   uint32_t bin_count[kRadix];
   uint32_t gbase[2][kRadix];  // destination of sorted position p = gbase[d] + p
@@ -357,6 +359,7 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
+      mbar_init(&S.kfull[s], 32);
       mbar_init(&S.full[s], 32);
       mbar_init(&S.empty[s], kWsWriteThreads);
     }
@@ -398,6 +401,7 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
       if (ch < 0) {
         if (lane == 0) ts.chunk = -1;
         __syncwarp();
+        mbar_arrive(&S.kfull[s]);
         mbar_arrive(&S.full[s]);
         drain_from = q - NS + 1;  // slot s now holds the end marker
         break;
@@ -437,37 +441,48 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
         ts.hi = ci.hi;
       }
       __syncwarp();
-      // unaligned edges with plain loads (the whole warp)
-      for (int r = 0; r < nrows; ++r) {
-        const RowPlan p = ts.row[r];
-        const int nplain = p.head + (n - p.tail_from);
-        uint8_t* dst = buf + (size_t)r * row_slot<T>(4) + p.off;
-        for (int x = lane; x < nplain; x += 32) {
-          const int i = x < p.head ? x : p.tail_from + (x - p.head);
-          if (r < c.order)
-            *reinterpret_cast<uint32_t*>(dst + (size_t)i * 4) =
-                (uint32_t)__ldg(c.in + (int64_t)r * c.in_stride + start + i);
-          else if (VB == 8)
-            *reinterpret_cast<unsigned long long*>(dst + (size_t)i * 8) =
-                __ldg(reinterpret_cast<const unsigned long long*>(c.vin) + start + i);
-          else
-            *reinterpret_cast<uint32_t*>(dst + (size_t)i * 4) =
-                __ldg(reinterpret_cast<const uint32_t*>(c.vin) + start + i);
-        }
-      }
-      // total bytes of the bulk copies, then one transaction-counted arrival
-      unsigned total = bytes;
+      // The rows the digit is read from (key rows) are staged first, under
+      // their own barrier, so ranking starts while the other rows still load.
+      unsigned kmask = 0;
+      for (int f = 0; f < ts.it.pd.nfields; ++f) kmask |= 1u << ts.it.pd.f[f].mode;
+      const bool is_key = lane < nrows && (kmask >> lane & 1u);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive_expect_tx(&S.full[s], total);
-      else mbar_arrive(&S.full[s]);
-      if (lane < nrows && bytes) {
-        const int e = lane < c.order ? 4 : VB;
-        bulk_g2s(buf + (size_t)lane * row_slot<T>(4) + rp.off + (size_t)rp.head * e,
-                 reinterpret_cast<const void*>(row_base(c, lane) + (uintptr_t)(start + rp.head) * e),
-                 bytes, &S.full[s]);
+      for (int phase = 0; phase < 2; ++phase) {
+        uint64_t* bar = phase == 0 ? &S.kfull[s] : &S.full[s];
+        // unaligned edges of this phase's rows with plain loads (the whole warp)
+        for (int r = 0; r < nrows; ++r) {
+          if (((kmask >> r) & 1u) != (phase == 0 ? 1u : 0u)) continue;
+          const RowPlan p = ts.row[r];
+          const int nplain = p.head + (n - p.tail_from);
+          uint8_t* dst = buf + (size_t)r * row_slot<T>(4) + p.off;
+          for (int x = lane; x < nplain; x += 32) {
+            const int i = x < p.head ? x : p.tail_from + (x - p.head);
+            if (r < c.order)
+              *reinterpret_cast<uint32_t*>(dst + (size_t)i * 4) =
+                  (uint32_t)__ldg(c.in + (int64_t)r * c.in_stride + start + i);
+            else if (VB == 8)
+              *reinterpret_cast<unsigned long long*>(dst + (size_t)i * 8) =
+                  __ldg(reinterpret_cast<const unsigned long long*>(c.vin) + start + i);
+            else
+              *reinterpret_cast<uint32_t*>(dst + (size_t)i * 4) =
+                  __ldg(reinterpret_cast<const uint32_t*>(c.vin) + start + i);
+          }
+        }
+        // bytes of this phase's bulk copies, then one transaction-counted arrival
+        const bool mine = lane < nrows && is_key == (phase == 0);
+        unsigned total = mine ? bytes : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_expect_tx(bar, total);
+        else mbar_arrive(bar);
+        if (mine && bytes) {
+          const int e = lane < c.order ? 4 : VB;
+          bulk_g2s(buf + (size_t)lane * row_slot<T>(4) + rp.off + (size_t)rp.head * e,
+                   reinterpret_cast<const void*>(row_base(c, lane) + (uintptr_t)(start + rp.head) * e),
+                   bytes, bar);
+        }
       }
       ++issued;
       // next work item
@@ -480,14 +495,16 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
     // a normal end these waits return at once; after a timeout elsewhere they
     // are bounded like every other wait.
     if (lane == 0)
-      for (int x = drain_from > 0 ? drain_from : 0; x < issued; ++x)
+      for (int x = drain_from > 0 ? drain_from : 0; x < issued; ++x) {
+        mbar_wait(&S.kfull[x % NS], (x / NS) & 1, status);
         mbar_wait(&S.full[x % NS], (x / NS) & 1, status);
+      }
   } else if (warp < kWsRankWarps) {
     // ---------------- rankers ----------------
     const int w = warp;
     for (int q = 0;; ++q) {
       const int s = q % NS, j = q & 1;
-      const bool okf = mbar_wait(&S.full[s], (q / NS) & 1, status);
+      const bool okf = mbar_wait(&S.kfull[s], (q / NS) & 1, status);
       const bool okc = q < 2 || mbar_wait(&S.consumed[j], ((q / 2) - 1) & 1, status);
       if (!(okf && okc)) S.rk_abort = 1;  // the writers stop without writing
       const TileSlot& ts = S.slot[s];
@@ -513,7 +530,8 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i)
         if (w * ITEMS * 32 + i * 32 + lane >= n_valid) dig[i] = kRadix - 1;  // padding sorts last
-      if (!block_rank<RW, ITEMS, 1>(dig, rank, S.warp_hist, S.bin_start, S.bin_count, go)) {
+      if (!block_rank<RW, ITEMS, 1>(dig, rank, S.warp_hist, S.bin_start, S.bin_count, S.rank_tmp,
+                                    go)) {
         mbar_arrive(&S.ranked[j]);  // the writers see the end marker (or the abort)
         break;
       }
@@ -543,6 +561,11 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
       if (!mbar_wait(&S.ranked[j], (q / 2) & 1, status)) break;
       const TileSlot& ts = S.slot[s];
       if (ts.chunk < 0 || S.rk_abort) break;
+      // every row of the tile has landed (the key rows, which the rankers
+      // waited for, and the others)
+      if (!mbar_wait(&S.kfull[s], (q / NS) & 1, status) ||
+          !mbar_wait(&S.full[s], (q / NS) & 1, status))
+        break;
       const uint8_t* buf = stage + (size_t)s * bufsz;
       const Cols& c = ts.it.c;
       const int n_valid = ts.end - ts.start, lo = ts.lo, hi = ts.hi;
@@ -622,6 +645,10 @@ cudaError_t launch_move_vb(const Cols& c, const LargeSegs& ls, const PassDesc& p
     if (ws_smem<4096, 3, VB, 16>(c.order) <= kMax) QSD_MV(4096, 3, 16, 15);
     QSD_MV(4096, 2, 16, 15);
   }
+  if (ls.tile == 3584) {
+    if (ws_smem<3584, 3, VB, 16>(c.order) <= kMax) QSD_MV(3584, 3, 16, 15);
+    QSD_MV(3584, 2, 16, 15);
+  }
   if (ls.tile == 2048) {
     if (ws_smem<2048, 3, VB, 16>(c.order) <= kMax) QSD_MV(2048, 3, 16, 15);
     QSD_MV(2048, 2, 16, 15);
@@ -633,19 +660,28 @@ cudaError_t launch_move_vb(const Cols& c, const LargeSegs& ls, const PassDesc& p
 
 }  // namespace
 
-// Entries per tile: the requested size (4096, 2048 or 1024) if its two-slot
-// ring fits 227 KB of shared memory, else the largest that fits.
+// Entries per tile. A requested size (4096, 3584, 2048 or 1024) is honoured
+// if its two-slot ring fits 227 KB of shared memory, else the next smaller
+// one that fits. Automatically: the largest of 4096 and 3584 entries whose
+// three-slot ring fits (a third slot lets the loads run two tiles ahead;
+// measured faster than two slots of a larger tile), else the largest tile
+// whose two-slot ring fits.
 int digit_tile(int order, int vbytes, int tile) {
-  auto fits = [&](int T, size_t hdr) {
-    const size_t rows = (size_t)order * (T * 4 + 16) + (vbytes ? (size_t)T * vbytes + 16 : 0);
-    return hdr + 2 * rows <= 227 * 1024;
+  auto rows = [&](int T) {
+    return (size_t)order * (T * 4 + 16) + (vbytes ? (size_t)T * vbytes + 16 : 0);
   };
-  const bool f4 = fits(4096, ws_header<4096, 2, 16>());
-  const bool f2 = fits(2048, ws_header<2048, 2, 16>());
+  constexpr size_t kMax = 227 * 1024;
+  const bool f4 = ws_header<4096, 2, 16>() + 2 * rows(4096) <= kMax;
+  const bool f35 = ws_header<3584, 2, 16>() + 2 * rows(3584) <= kMax;
+  const bool f2 = ws_header<2048, 2, 16>() + 2 * rows(2048) <= kMax;
   if (tile == 4096 && f4) return 4096;
-  if ((tile == 2048 || tile == 4096) && f2) return 2048;
-  if (tile == 1024) return 1024;
+  if ((tile == 3584 || tile == 4096) && f35) return 3584;
+  if ((tile == 2048 || tile == 3584 || tile == 4096) && f2) return 2048;
+  if (tile != 0) return 1024;
+  if (ws_header<4096, 3, 16>() + 3 * rows(4096) <= kMax) return 4096;
+  if (ws_header<3584, 3, 16>() + 3 * rows(3584) <= kMax) return 3584;
   if (f4) return 4096;
+  if (f35) return 3584;
   if (f2) return 2048;
   return 1024;
 }

@@ -183,7 +183,7 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
         }
         dig[i] = d;
       }
-      block_rank<kLsWarps, ITEMS>(dig, rank, S.warp_hist, S.bin_start, S.bin_count);
+      block_rank<kLsWarps, ITEMS>(dig, rank, S.warp_hist, S.bin_start, S.bin_count, S.tmp);
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) S.perm[cur ^ 1][rank[i]] = (uint16_t)el[i];
       __syncthreads();

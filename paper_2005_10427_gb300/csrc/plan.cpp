@@ -96,7 +96,7 @@ qsd_status qsd_plan_ex(int order, const int64_t* dims,
       o.local_capacity != 2048 && o.local_capacity != 4096 &&
       o.local_capacity != 8192)
     return QSD_ERR_INVALID_ARGUMENT;
-  if (o.tile != 0 && o.tile != 1024 && o.tile != 2048 && o.tile != 4096)
+  if (o.tile != 0 && o.tile != 1024 && o.tile != 2048 && o.tile != 3584 && o.tile != 4096)
     return QSD_ERR_INVALID_ARGUMENT;
   if (o.chunk_tiles < 0 || o.chunk_tiles > 256) return QSD_ERR_INVALID_ARGUMENT;
 

@@ -150,6 +150,16 @@ def test_digit_widths(qsd, digit_bits):
         check(qsd, coords, vals, dims, sigma, digit_bits=digit_bits)
 
 
+@pytest.mark.parametrize("tile,chunk_tiles", [(1024, 8), (2048, 3), (3584, 8), (3584, 1),
+                                              (4096, 8), (4096, 16)])
+def test_tile_sizes_and_chunk_lengths(qsd, tile, chunk_tiles):
+    # ragged tiles and chunks inside large Zipf buckets and a global group
+    dims = [40, 3000, 700]
+    coords, vals = tensor(dims, 150_000, seed=tile + chunk_tiles, zipf=1.1)
+    for sigma in [(0, 2, 1), (2, 1, 0)]:
+        check(qsd, coords, vals, dims, sigma, tile=tile, chunk_tiles=chunk_tiles)
+
+
 @pytest.mark.parametrize("cap", [1024, 2048, 4096, 8192])
 def test_local_capacities(qsd, cap):
     dims = [3000, 500, 700]
