@@ -88,7 +88,8 @@ qsd_status batch_prepare(BatchCore& b) {
     }
     if (t.nnz > 0 && eff[i].empty()) b.copies.push_back(i);
   }
-  b.C = b.opts.local_capacity ? b.opts.local_capacity : 4096;
+  b.C = local_sort_capacity(b.opts.local_capacity ? b.opts.local_capacity : 4096, b.max_order,
+                            b.vbytes);
   b.T = digit_tile(b.max_order, b.vbytes, b.opts.tile);
   b.CH = digit_chunk(b.max_order, b.vbytes, b.opts.tile, b.opts.chunk_tiles);
   const int seg_tile = seg_tile_entries();

@@ -154,8 +154,11 @@ __device__ __forceinline__ uint32_t field_bits(uint32_t c, const DigitField& f) 
 // consecutive ranges and each warp's rounds consecutive 32-element pieces.
 // On return rank[i] is the element's position when the tile is stably sorted
 // by digit; s_bin_start[d] / s_bin_count[d] give each digit's run.
-// Ranking inside a round uses __match_any_sync (lanes with equal digits) and
-// a per-warp running count in shared memory.
+// Inside a round, the lanes holding equal digits are found from eight
+// ballots, one per digit bit (a lane's peers are the lanes that agree with it
+// on every bit): a fixed cost, where a warp match instruction's cost grows
+// with the number of distinct digits in the warp (measured on this GPU).
+// A per-warp running count per digit in shared memory orders the rounds.
 // Barrier over the first NTHREADS threads: the whole block when BAR == 0,
 // else named barrier BAR.
 template <int BAR, int NTHREADS>
@@ -182,11 +185,24 @@ __device__ __forceinline__ bool group_all(bool pred) {
   return r != 0;
 }
 
-// Counts fit 16 bits (a tile has at most 65535 entries). With BAR != 0 the
-// ranking threads are the first NWARPS warps of the block and synchronise on
-// named barrier BAR only (other warps of the block may be doing other work).
-// Returns whether `ok` held on every ranking thread (reduced at the ranking's
-// first barrier, so a group can agree to stop at no extra cost).
+// Lanes of the warp whose 8-bit digit equals this lane's: the AND over the
+// digit's bits of the ballot of that bit (or of its complement).
+__device__ __forceinline__ uint32_t warp_peers(uint32_t d) {
+  uint32_t m = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < kRadixBits; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+    m &= bit ? bal : ~bal;
+  }
+  return m;
+}
+
+// With BAR != 0 the ranking threads are the first NWARPS warps of the block
+// and synchronise on named barrier BAR only (other warps of the block may be
+// doing other work). Returns whether `ok` held on every ranking thread
+// (reduced at the ranking's first barrier, so a group can agree to stop at
+// no extra cost).
 //
 // After the per-warp counts, one block-wide exclusive scan over the counters
 // taken digit-major (digit d's counters of warps 0..NWARPS-1, then digit d+1's)
@@ -197,7 +213,7 @@ __device__ __forceinline__ bool group_all(bool pred) {
 template <int NWARPS, int ITEMS, int BAR = 0>
 __device__ __forceinline__ bool block_rank(const uint32_t (&dig)[ITEMS],
                                            uint32_t (&rank)[ITEMS],
-                                           uint16_t* s_warp_hist,  // [NWARPS][kRadix]
+                                           uint32_t* s_warp_hist,  // [NWARPS][kRadix]
                                            uint32_t* s_bin_start,  // [kRadix]
                                            uint32_t* s_bin_count,  // [kRadix]
                                            uint32_t* s_tmp,        // [NWARPS]
@@ -207,17 +223,14 @@ __device__ __forceinline__ bool block_rank(const uint32_t (&dig)[ITEMS],
   constexpr int TPD = NWARPS / 8;  // scanning threads per digit
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
-  uint16_t* h = s_warp_hist + w * kRadix;
-  // the warp's 16-bit counters, two digits per 32-bit word
-  uint32_t* h32 = reinterpret_cast<uint32_t*>(h);
+  uint32_t* h = s_warp_hist + w * kRadix;  // the warp's counters, then its offsets
 #pragma unroll
-  for (int k = lane; k < kRadix / 2; k += 32) h32[k] = 0;
+  for (int k = lane; k < kRadix; k += 32) h[k] = 0;
   __syncwarp();
   const uint32_t lt = (1u << lane) - 1u;
-  // lanes with equal digits, for every round at once
   uint32_t peers[ITEMS];
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) peers[i] = __match_any_sync(0xffffffffu, dig[i]);
+  for (int i = 0; i < ITEMS; ++i) peers[i] = warp_peers(dig[i]);
   // one leader per digit and round adds the round's count to the warp's
   // counter; shared atomics of one warp to one address apply in issue order,
   // so each round sees the counts of the rounds before it
@@ -225,14 +238,11 @@ __device__ __forceinline__ bool block_rank(const uint32_t (&dig)[ITEMS],
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     old[i] = 0;
-    if (lane == __ffs(peers[i]) - 1)
-      old[i] = atomicAdd(&h32[dig[i] >> 1], (uint32_t)__popc(peers[i]) << ((dig[i] & 1u) * 16));
+    if (lane == __ffs(peers[i]) - 1) old[i] = atomicAdd(&h[dig[i]], (uint32_t)__popc(peers[i]));
   }
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const uint32_t o = __shfl_sync(0xffffffffu, old[i], __ffs(peers[i]) - 1);
-    rank[i] = ((o >> ((dig[i] & 1u) * 16)) & 0xffffu) + __popc(peers[i] & lt);
-  }
+  for (int i = 0; i < ITEMS; ++i)
+    rank[i] = __shfl_sync(0xffffffffu, old[i], __ffs(peers[i]) - 1) + __popc(peers[i] & lt);
   bool all_ok;
   if constexpr (BAR == 0)
     all_ok = __syncthreads_and(ok) != 0;
@@ -256,6 +266,7 @@ __device__ __forceinline__ bool block_rank(const uint32_t (&dig)[ITEMS],
     if (lane >= o) incl += y;
   }
   if (lane == 31) s_tmp[w] = incl;
+  // every counter has been read: from here the same words hold offsets
   group_sync<BAR, NWARPS * 32>();
   uint32_t wt = lane < NWARPS ? s_tmp[lane] : 0u;
 #pragma unroll
@@ -270,7 +281,7 @@ __device__ __forceinline__ bool block_rank(const uint32_t (&dig)[ITEMS],
   if (part == 0) s_bin_start[d] = prefix;
   if (part == TPD - 1) s_bin_count[d] = prefix + local - (TPD > 1 ? dstart : prefix);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) s_warp_hist[(w0 + k) * kRadix + d] = (uint16_t)(prefix + c[k]);
+  for (int k = 0; k < 8; ++k) s_warp_hist[(w0 + k) * kRadix + d] = prefix + c[k];
   group_sync<BAR, NWARPS * 32>();
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) rank[i] += h[dig[i]];

@@ -296,6 +296,7 @@ struct RowPlan {
 
 // One unit of work: tile `k` of chunk `chunk` (chunk >= nchunks: the end).
 struct TileSlot {
+  alignas(16) uint32_t off0[kRadix];  // first tile of a chunk: the chunk's first slot per digit
   int chunk, k, ntile, start, end, lo, hi;
   RowPlan row[kMaxRows];
   PassTensor it;  // the chunk's tensor: buffers and digit
@@ -310,7 +311,7 @@ struct WsShared {
   uint64_t consumed[2];  // writers -> rankers: destinations used
   TileSlot slot[NS];
   uint32_t off[kRadix];  // rankers: running output slot per digit of the chunk
-  uint16_t warp_hist[RW * kRadix];
+  uint32_t warp_hist[RW * kRadix];
   uint32_t rank_tmp[RW];  // block_rank's scan scratch
   uint32_t bin_start[kRadix];
   uint32_t bin_count[kRadix];
@@ -473,10 +474,15 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
         unsigned total = mine ? bytes : 0u;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+        // a chunk's first tile also brings the chunk's output offsets (1 KB)
+        const bool offs = phase == 0 && k == 0;
+        if (offs) total += kRadix * sizeof(uint32_t);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive_expect_tx(bar, total);
         else mbar_arrive(bar);
+        if (offs && lane == 31)
+          bulk_g2s(ts.off0, chunk_off + (size_t)ch * kRadix, kRadix * sizeof(uint32_t), bar);
         if (mine && bytes) {
           const int e = lane < c.order ? 4 : VB;
           bulk_g2s(buf + (size_t)lane * row_slot<T>(4) + rp.off + (size_t)rp.head * e,
@@ -535,12 +541,10 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
         mbar_arrive(&S.ranked[j]);  // the writers see the end marker (or the abort)
         break;
       }
-      const int ch = ts.chunk;
       const PassDesc& pd = ts.it.pd;
       const int nbins = 1 << pd.bits;
-      if (ts.k == 0)  // a new chunk: its first output slot per digit
-        for (int d = threadIdx.x; d < nbins; d += kWsRankThreads)
-          S.off[d] = chunk_off[(size_t)ch * kRadix + d];
+      if (ts.k == 0)  // a new chunk: its first output slot per digit (staged with the tile)
+        for (int d = threadIdx.x; d < nbins; d += kWsRankThreads) S.off[d] = ts.off0[d];
       for (int d = threadIdx.x; d < nbins; d += kWsRankThreads) {
         uint32_t cnt = S.bin_count[d];
         if (d == kRadix - 1) cnt -= (uint32_t)(T - n_valid);

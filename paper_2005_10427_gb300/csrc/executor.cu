@@ -48,7 +48,7 @@ Layout layout_for(const qsd_plan_s* p, int64_t nnz, int vbytes) {
   Layout L;
   std::memset(&L, 0, sizeof(L));
   const int CH = digit_chunk(p->order, vbytes, p->opts.tile, p->opts.chunk_tiles);
-  const int C = p->local_capacity;
+  const int C = local_sort_capacity(p->local_capacity, p->order, vbytes);
   int maxp = 0;
   for (int g = 0; g < p->ngroups; ++g) maxp = std::max(maxp, p->groups[g].npasses);
   L.max_passes = std::max(maxp, 1);
@@ -179,7 +179,7 @@ qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
   const int vb = has_vals ? vals->elem_bytes : 0;
   const int T = digit_tile(plan->order, vb, plan->opts.tile);
   const int CH = digit_chunk(plan->order, vb, plan->opts.tile, plan->opts.chunk_tiles);
-  const int C = plan->local_capacity;
+  const int C = local_sort_capacity(plan->local_capacity, plan->order, vb);
   // one tensor: no batch tables
   PassBatch pb1;
   std::memset(&pb1, 0, sizeof(pb1));

@@ -164,7 +164,11 @@ cudaError_t launch_digit_move(const Cols& c, const LargeSegs& ls, const PassDesc
                               const uint32_t* chunk_off, int* claim, int max_chunks,
                               unsigned* status, const PassBatch& pb, cudaStream_t stream);
 
-// With a batch (lb.n > 0) `c` only gives the value width and `pl` is unused.
+// The bucket capacity the shared-memory sort runs with: the largest power of
+// two in [1024, want] whose staged rows fit shared memory.
+int local_sort_capacity(int want, int order, int vbytes);
+// With a batch (lb.n > 0) `c` gives the staging layout (largest order, value
+// width) and `pl` is unused.
 cudaError_t launch_local_sort(const Cols& c, const PassList& pl,
                               const int* seg_start, const int* counters,
                               int single, int nnz, int capacity,

@@ -4,17 +4,18 @@
 // never leave their bucket, so each processor sorts the buckets that begin
 // in its region. Here each thread block owns a window of `CAP` entries and
 // sorts the small buckets (at most CAP entries each) that begin in it, in
-// batches of consecutive buckets that fit shared memory together. A batch is
-// stably sorted by (bucket, key): least-significant-digit-first radix passes
-// over the group's key digits, then over the bucket index -- the order
-// Algorithm 2 uses (sort on the mode, then stably re-bucket) -- each pass a
-// stable ranking in shared memory. Only a permutation of batch positions is
-// sorted; each coordinate row and the values then move once: the row's batch
-// range is staged in shared memory and written back permuted with coalesced
-// stores, so the kernel may write its output over its input. In a batch
-// round the buckets of several tensors share the index space; a batch of
-// buckets never crosses from one tensor into the next, and each takes its
-// tensor's rows and digits.
+// batches of consecutive buckets that fit shared memory together. A batch's
+// rows are staged in shared memory by bulk asynchronous copies (unaligned
+// edges by plain loads) while the block numbers the batch's buckets; the
+// batch is then stably sorted by (bucket, key): least-significant-digit-first
+// radix passes over the group's key digits, then over the bucket index -- the
+// order Algorithm 2 uses (sort on the mode, then stably re-bucket) -- each
+// pass a stable ranking in shared memory of a permutation of batch
+// positions, reading the digits from the staged rows. Every row is then
+// written back through the permutation with coalesced stores, so the kernel
+// may write its output over its input. In a batch round the buckets of
+// several tensors share the index space; a batch of buckets never crosses
+// from one tensor into the next, and each takes its tensor's rows and digits.
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -38,7 +39,7 @@ struct LsVal<8> {
 
 template <int CAP>
 struct LsShared {
-  uint16_t warp_hist[kLsWarps * kRadix];
+  uint32_t warp_hist[kLsWarps * kRadix];
   uint32_t bin_start[kRadix];
   uint32_t bin_count[kRadix];
   uint32_t tmp[kLsWarps + 1];
@@ -48,7 +49,17 @@ struct LsShared {
   Cols c;                  // the current batch's tensor: rows
   const PassDesc* passes;  // and key passes
   int npasses;
+  uint64_t ld;             // the batch's staged rows have landed
+  int row_off[kMaxOrder + 1];   // byte offset of element 0 in each staged row
+  int row_head[kMaxOrder + 1];  // elements [0, head) and [tail, n) come by plain loads
+  int row_tail[kMaxOrder + 1];
 };
+
+template <int CAP>
+size_t ls_smem(int order, int vbytes) {
+  return ((sizeof(LsShared<CAP>) + 15) & ~size_t(15)) + (size_t)order * ((size_t)CAP * 4 + 16) +
+         (vbytes ? (size_t)CAP * vbytes + 16 : 0);
+}
 
 // First index i in [lo, hi) with a[i] > x (or hi).
 __device__ __forceinline__ int upper_bound_i(const int* a, int lo, int hi, int x) {
@@ -70,11 +81,14 @@ __device__ __forceinline__ int lower_bound_i(const int* a, int lo, int hi, int x
 template <int CAP, int VB>
 __global__ void __launch_bounds__(kLsThreads)
 k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict__ seg_start,
-             const int* __restrict__ counters, int single, int nnz, LsBatch lb) {
+             const int* __restrict__ counters, int single, int nnz, LsBatch lb, int lay_order,
+             unsigned* status) {
   constexpr int ITEMS = CAP / kLsThreads;
+  constexpr size_t kRow4 = (size_t)CAP * 4 + 16;  // a staged coordinate row
   extern __shared__ __align__(16) uint8_t smem[];
   LsShared<CAP>& S = *reinterpret_cast<LsShared<CAP>*>(smem);
   uint8_t* stage = smem + ((sizeof(LsShared<CAP>) + 15) & ~size_t(15));
+  uint8_t* const vstage = stage + (size_t)lay_order * kRow4;  // the value row
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int win0 = blockIdx.x * CAP;
   if (win0 >= nnz) return;
@@ -82,6 +96,7 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
   const int nseg = single ? 1 : counters[kCntNumSeg];
 
   if (threadIdx.x == 0) {
+    mbar_init(&S.ld, 1);
     S.c = c1;
     S.passes = pl.pass;
     S.npasses = pl.npasses;
@@ -96,6 +111,7 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
   __syncthreads();
   const int last = S.last;
   int s = S.first;
+  unsigned phase = 0;
   while (s < last) {
     if (threadIdx.x == 0) {
       const int a = single ? 0 : seg_start[s];
@@ -133,8 +149,48 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
     const int A = single ? 0 : seg_start[s];
     const int n = (single ? nnz : seg_start[e]) - A;
     const int nsb = e - s;
+    const int nrows = c.order + (VB ? 1 : 0);
+    auto row_smem = [&](int r) -> uint8_t* { return r < c.order ? stage + (size_t)r * kRow4 : vstage; };
+    auto row_gmem = [&](int r) -> uintptr_t {
+      return r < c.order ? reinterpret_cast<uintptr_t>(c.in + (int64_t)r * c.in_stride + A)
+                         : reinterpret_cast<uintptr_t>(c.vin) + (uintptr_t)A * VB;
+    };
 
-    // Bucket index of every batch position (marks at bucket starts, scanned).
+    // Stage the batch's rows: warp 0 starts one bulk copy per row for its
+    // 16-byte-aligned body (lane r: row r).
+    if (w == 0) {
+      fence_proxy_async_smem();  // the previous batch's reads of the stage came first
+      unsigned bytes = 0;
+      int head = 0;
+      if (lane < nrows) {
+        const int es = lane < c.order ? 4 : VB;
+        const uintptr_t g0 = row_gmem(lane), g1 = g0 + (uintptr_t)n * es;
+        const uintptr_t a0 = (g0 + 15) & ~uintptr_t(15), a1 = g1 & ~uintptr_t(15);
+        S.row_off[lane] = (int)(g0 & 15);
+        if (a1 > a0) {
+          head = (int)((a0 - g0) / es);
+          S.row_head[lane] = head;
+          S.row_tail[lane] = (int)((a1 - g0) / es);
+          bytes = (unsigned)(a1 - a0);
+        } else {
+          S.row_head[lane] = n;
+          S.row_tail[lane] = n;
+        }
+      }
+      unsigned total = bytes;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+      if (lane == 0) mbar_arrive_expect_tx(&S.ld, total);
+      __syncwarp();
+      if (lane < nrows && bytes) {
+        const int es = lane < c.order ? 4 : VB;
+        bulk_g2s(row_smem(lane) + S.row_off[lane] + (size_t)head * es,
+                 reinterpret_cast<const void*>(row_gmem(lane) + (uintptr_t)head * es), bytes, &S.ld);
+      }
+    }
+
+    // Bucket index of every batch position (marks at bucket starts, scanned),
+    // while the rows load.
     if (nsb > 1) {
       for (int i = threadIdx.x; i < CAP; i += kLsThreads) S.segid[i] = 0;
       __syncthreads();
@@ -156,7 +212,24 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
       }
     }
     for (int i = threadIdx.x; i < CAP; i += kLsThreads) S.perm[0][i] = (uint16_t)i;
+    __syncthreads();  // the row plans are visible
+    // unaligned edges with plain loads
+    for (int r = 0; r < nrows; ++r) {
+      const int head = S.row_head[r], tail = S.row_tail[r], np = head + (n - tail);
+      uint8_t* dst = row_smem(r) + S.row_off[r];
+      const uintptr_t src = row_gmem(r);
+      for (int x = threadIdx.x; x < np; x += kLsThreads) {
+        const int i = x < head ? x : tail + (x - head);
+        if (r < c.order || VB == 4)
+          reinterpret_cast<uint32_t*>(dst)[i] = __ldg(reinterpret_cast<const uint32_t*>(src) + i);
+        else
+          reinterpret_cast<unsigned long long*>(dst)[i] =
+              __ldg(reinterpret_cast<const unsigned long long*>(src) + i);
+      }
+    }
     __syncthreads();
+    mbar_wait(&S.ld, phase, status);  // the bulk copies have landed
+    phase ^= 1u;
 
     int cur = 0;
     int seg_bits = 0;
@@ -175,7 +248,9 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
             d = 0;
             for (int k = 0; k < pd.nfields; ++k) {
               const DigitField f = pd.f[k];
-              d |= field_bits((uint32_t)__ldg(c.in + (int64_t)f.mode * c.in_stride + A + el[i]), f);
+              const uint32_t* row =
+                  reinterpret_cast<const uint32_t*>(row_smem(f.mode) + S.row_off[f.mode]);
+              d |= field_bits(row[el[i]], f);
             }
           } else {
             d = ((uint32_t)S.segid[el[i]] >> ((p - key_passes) * kRadixBits)) & (kRadix - 1);
@@ -190,26 +265,19 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
       cur ^= 1;
     }
 
-    // Move the rows: stage the batch range, write it back permuted.
-    uint32_t* st32 = reinterpret_cast<uint32_t*>(stage);
+    // Every row back through the permutation (coalesced stores).
     for (int m = 0; m < c.order; ++m) {
-      const int32_t* src = c.in + (int64_t)m * c.in_stride + A;
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(row_smem(m) + S.row_off[m]);
       int32_t* dst = c.out + (int64_t)m * c.out_stride + A;
-      for (int i = threadIdx.x; i < n; i += kLsThreads) st32[i] = (uint32_t)src[i];
-      __syncthreads();
-      for (int i = threadIdx.x; i < n; i += kLsThreads) dst[i] = (int32_t)st32[S.perm[cur][i]];
-      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += kLsThreads) dst[i] = (int32_t)src[S.perm[cur][i]];
     }
     if constexpr (VB != 0) {
       using T = typename LsVal<VB>::T;
-      const T* src = reinterpret_cast<const T*>(c.vin) + A;
+      const T* src = reinterpret_cast<const T*>(vstage + S.row_off[c.order]);
       T* dst = reinterpret_cast<T*>(c.vout) + A;
-      T* stv = reinterpret_cast<T*>(stage);
-      for (int i = threadIdx.x; i < n; i += kLsThreads) stv[i] = src[i];
-      __syncthreads();
-      for (int i = threadIdx.x; i < n; i += kLsThreads) dst[i] = stv[S.perm[cur][i]];
-      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += kLsThreads) dst[i] = src[S.perm[cur][i]];
     }
+    __syncthreads();  // the stage is free for the next batch
     s = e;
   }
 }
@@ -217,9 +285,10 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
 template <int CAP, int VB>
 cudaError_t launch_ls(const Cols& c, const PassList& pl, const int* seg_start,
                       const int* counters, int single, int nnz, const LsBatch& lb,
-                      cudaStream_t stream) {
-  const size_t smem = ((sizeof(LsShared<CAP>) + 15) & ~size_t(15)) +
-                      (size_t)CAP * (VB == 8 ? 8 : 4);
+                      unsigned* status, cudaStream_t stream) {
+  // shared state, then the staged rows: c.order coordinate rows (the largest
+  // order of a batch) and the value row
+  const size_t smem = ls_smem<CAP>(c.order, VB);
   cudaError_t e = cudaFuncSetAttribute(k_local_sort<CAP, VB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -227,33 +296,42 @@ cudaError_t launch_ls(const Cols& c, const PassList& pl, const int* seg_start,
   const int grid = single ? 1 : (nnz + CAP - 1) / CAP;
   if (grid < 1) return cudaSuccess;
   k_local_sort<CAP, VB><<<grid, kLsThreads, smem, stream>>>(c, pl, seg_start, counters,
-                                                            single, nnz, lb);
+                                                            single, nnz, lb, c.order, status);
   return cudaGetLastError();
 }
 
 template <int CAP>
 cudaError_t launch_ls_cap(const Cols& c, const PassList& pl, const int* seg_start,
                           const int* counters, int single, int nnz, const LsBatch& lb,
-                          cudaStream_t stream) {
+                          unsigned* status, cudaStream_t stream) {
   switch (c.vbytes) {
-    case 0: return launch_ls<CAP, 0>(c, pl, seg_start, counters, single, nnz, lb, stream);
-    case 4: return launch_ls<CAP, 4>(c, pl, seg_start, counters, single, nnz, lb, stream);
-    case 8: return launch_ls<CAP, 8>(c, pl, seg_start, counters, single, nnz, lb, stream);
+    case 0: return launch_ls<CAP, 0>(c, pl, seg_start, counters, single, nnz, lb, status, stream);
+    case 4: return launch_ls<CAP, 4>(c, pl, seg_start, counters, single, nnz, lb, status, stream);
+    case 8: return launch_ls<CAP, 8>(c, pl, seg_start, counters, single, nnz, lb, status, stream);
   }
   return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
+// The largest bucket capacity (a power of two in [1024, want]) whose staged
+// rows fit 227 KB of shared memory at this order and value width.
+int local_sort_capacity(int want, int order, int vbytes) {
+  constexpr size_t kMax = 227 * 1024;
+  if (want >= 8192 && ls_smem<8192>(order, vbytes) <= kMax) return 8192;
+  if (want >= 4096 && ls_smem<4096>(order, vbytes) <= kMax) return 4096;
+  if (want >= 2048 && ls_smem<2048>(order, vbytes) <= kMax) return 2048;
+  return 1024;
+}
+
 cudaError_t launch_local_sort(const Cols& c, const PassList& pl, const int* seg_start,
                               const int* counters, int single, int nnz, int capacity,
                               unsigned* status, const LsBatch& lb, cudaStream_t stream) {
-  (void)status;
   switch (capacity) {
-    case 1024: return launch_ls_cap<1024>(c, pl, seg_start, counters, single, nnz, lb, stream);
-    case 2048: return launch_ls_cap<2048>(c, pl, seg_start, counters, single, nnz, lb, stream);
-    case 4096: return launch_ls_cap<4096>(c, pl, seg_start, counters, single, nnz, lb, stream);
-    case 8192: return launch_ls_cap<8192>(c, pl, seg_start, counters, single, nnz, lb, stream);
+    case 1024: return launch_ls_cap<1024>(c, pl, seg_start, counters, single, nnz, lb, status, stream);
+    case 2048: return launch_ls_cap<2048>(c, pl, seg_start, counters, single, nnz, lb, status, stream);
+    case 4096: return launch_ls_cap<4096>(c, pl, seg_start, counters, single, nnz, lb, status, stream);
+    case 8192: return launch_ls_cap<8192>(c, pl, seg_start, counters, single, nnz, lb, status, stream);
   }
   return cudaErrorInvalidValue;
 }
