@@ -86,7 +86,10 @@ typedef struct {
                             0 = automatic */
   int local_capacity;    /* largest bucket (entries) sorted in shared memory
                             by one thread block, a power of two in
-                            [1024, 8192]; 0 = automatic */
+                            [1024, 8192]; 0 = automatic (4096). The library
+                            lowers it when the staged rows of the tensor's
+                            order and value width would leave room for fewer
+                            than two blocks per SM */
   int no_skip;           /* nonzero: ignore the input ordering and run a full
                             radix sort over every mode (the baseline of
                             Section 3 that the method improves on) */

@@ -314,13 +314,19 @@ cudaError_t launch_ls_cap(const Cols& c, const PassList& pl, const int* seg_star
 
 }  // namespace
 
-// The largest bucket capacity (a power of two in [1024, want]) whose staged
-// rows fit 227 KB of shared memory at this order and value width.
+// The bucket capacity the sort runs with: the largest power of two in
+// [1024, want] whose staged rows leave room for two blocks per SM (the
+// loads of one block overlap the ranking of the other), else the largest
+// that fits shared memory at all.
 int local_sort_capacity(int want, int order, int vbytes) {
-  constexpr size_t kMax = 227 * 1024;
-  if (want >= 8192 && ls_smem<8192>(order, vbytes) <= kMax) return 8192;
-  if (want >= 4096 && ls_smem<4096>(order, vbytes) <= kMax) return 4096;
-  if (want >= 2048 && ls_smem<2048>(order, vbytes) <= kMax) return 2048;
+  constexpr size_t kMax = 227 * 1024, kTwo = 113 * 1024;
+  const size_t sz[4] = {ls_smem<8192>(order, vbytes), ls_smem<4096>(order, vbytes),
+                        ls_smem<2048>(order, vbytes), ls_smem<1024>(order, vbytes)};
+  const int cap[4] = {8192, 4096, 2048, 1024};
+  for (int k = 0; k < 4; ++k)
+    if (cap[k] <= want && sz[k] <= kTwo) return cap[k];
+  for (int k = 0; k < 4; ++k)
+    if (cap[k] <= want && sz[k] <= kMax) return cap[k];
   return 1024;
 }
 
