@@ -209,6 +209,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="batched run without autotuning")
     ap.add_argument("--batched-steps", type=int, default=0,
                     help="timed runs of the batched workload (default: steps, 5..20)")
+    ap.add_argument("--no-csf", action="store_true", help="skip the CSF-levels measurement")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the Poisson-stream serving measurement")
     args = ap.parse_args()
@@ -333,6 +334,8 @@ def main():
                "h2d_bytes_per_step": len(plans) * nnz * R,
                "d2h_bytes_per_step": len(plans) * nnz * R}
 
+    csf = bench_csf(qsd, t, plans, perms, cb, vbuf, ws, stream) if not args.no_csf else None
+
     batched = None
     if not args.no_batched:
         del cb, vbuf
@@ -374,6 +377,8 @@ def main():
                                 "share": round(a["ms"] / total_ms, 4) if total_ms else None}
                             for k, a in sorted(agg.items(), key=lambda kv: -kv[1]["ms"])},
                 "clocks": clocks}
+        if csf is not None:
+            line["csf"] = csf
         if batched is not None:
             line["batched"] = batched
         if serving is not None:
@@ -555,6 +560,39 @@ def bench_serving(qsd, dev, budget_gb: float = 40.0, n_requests: int = 10_000,
             "peak_budget_gb": round(stats["peak_bytes"] / (1 << 30), 3),
             "alone_vs_mix_checked": len(kept), "alone_vs_mix_identical": bool(same),
             "pool_gen_seconds": round(gen_s, 1)}
+
+
+def bench_csf(qsd, t, plans, perms, cb, vbuf, ws, stream, reps: int = 5):
+    """CSF levels of each transposed output (qsd_csf_build): device time per
+    build, entries per second, and DRAM-side bytes of the two sweeps (every
+    coordinate row read twice) plus the node arrays written."""
+    r, nnz = t.coords.shape
+    dev = t.coords.device
+    ids = [torch.empty(nnz, dtype=torch.int32, device=dev) for _ in range(r)]
+    ptr = [torch.empty(2 if l == 0 else nnz + 1, dtype=torch.int32, device=dev)
+           for l in range(r + 1)]
+    nodes = torch.empty(r + 1, dtype=torch.int32, device=dev)
+    cws = torch.empty(qsd.csf_workspace_bytes(r, nnz), dtype=torch.uint8, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per = {}
+    for p, sigma in zip(plans, perms):
+        sel = qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, p, ws, stream)
+        rows = cb[sel]
+        for _ in range(2):
+            qsd.csf_build(rows, sigma, ids, ptr, nodes, cws, stream)
+        ev0.record(stream)
+        for _ in range(reps):
+            qsd.csf_build(rows, sigma, ids, ptr, nodes, cws, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / reps
+        n = [int(x) for x in nodes.cpu()]
+        written = 4 * (sum(n[1:]) + sum(n) + 1 + r)  # ids and ptr entries
+        per["".join(map(str, sigma))] = {
+            "ms": round(ms, 4), "gnnz_s": round(nnz / (ms / 1e3) / 1e9, 2),
+            "nodes": n, "gb_s": round((2 * 4 * r * nnz + written) / (ms / 1e3) / 1e9, 1)}
+    return {"what": "CSF levels of each transposed output (count, scan, write over the entries)",
+            "per_order": per}
 
 
 def sampled_check(qsd, t, plans, perms, cb, vbuf, ws, stream):

@@ -233,6 +233,34 @@ qsd_status qsd_workspace_status(const void* workspace, void* stream,
  * status word, which every transpose on that device ORs its errors into. */
 qsd_status qsd_get_async_status(void* stream, qsd_status* out);
 
+/* ---- Compressed sparse fiber levels ----
+ * The CSF tree of Section 2.1 for a tensor sorted under sigma (for example a
+ * result of qsd_transpose with target_perm sigma): level l (1..order) has one
+ * node per maximal run of entries with equal coordinates in modes
+ * sigma[0..l-1], in order. Level l's node ids are the coordinates of mode
+ * sigma[l-1]; node k of level l < order has children ptr[l][k] ..
+ * ptr[l][k+1]-1 on level l+1 (level 0 is the root); leaf k covers entries
+ * ptr[order][k] .. ptr[order][k+1]-1 (more than one only for duplicate
+ * coordinates), which index the values array. All arrays are device int32. */
+typedef struct {
+  int32_t* ids[QSD_MAX_ORDER];      /* ids[l]: level l+1's node ids, capacity >= nnz */
+  int32_t* ptr[QSD_MAX_ORDER + 1];  /* ptr[0]: capacity 2; ptr[l], l >= 1: capacity >= nnz + 1 */
+} qsd_csf;
+
+/* Device scratch (bytes) qsd_csf_build needs. */
+qsd_status qsd_csf_workspace_bytes(int order, int64_t nnz, size_t* bytes);
+
+/* Builds the CSF levels of the device rows `coords` (mode m at
+ * coords + m * stride, sorted under sigma) on `stream`: fills out->ids[0..order-1],
+ * out->ptr[0..order] and nodes[0..order] (device int32; nodes[l] = nodes on
+ * level l, nodes[0] = 1). One count, scan and write pass over the entries.
+ * Unsorted input gives a tree of the runs it does have (no error, every
+ * write in bounds). Errors: QSD_ERR_INVALID_ARGUMENT, QSD_ERR_UNSUPPORTED,
+ * QSD_ERR_WORKSPACE_TOO_SMALL, QSD_ERR_CUDA. */
+qsd_status qsd_csf_build(const int32_t* coords, int64_t stride, int64_t nnz, int order,
+                         const int* sigma, const qsd_csf* out, int32_t* nodes,
+                         void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---- Batches ----
  * Many independent tensors transposed together. The paper transposes one
  * tensor at a time; a batch runs the same method (each tensor gets its own

@@ -16,7 +16,8 @@ from typing import List, Optional, Sequence, Tuple
 
 from . import _capi
 
-__all__ = ["Plan", "QsdError", "Batch", "Server", "server_clock", "transpose", "transpose_buffers", "transpose_from",
+__all__ = ["Plan", "QsdError", "Batch", "Server", "server_clock", "csf_levels", "csf_build",
+           "csf_workspace_bytes", "transpose", "transpose_buffers", "transpose_from",
            "transpose_host", "transpose_noalloc", "tune_cache_save", "tune_cache_load",
            "get_async_status", "workspace_status", "build", "lib", "LIB_PATH"]
 
@@ -298,6 +299,54 @@ class Batch:
                                         int(workspace.numel()), _stream_handle(stream),
                                         int(reps), ctypes.byref(o)), "qsd_batch_tune")
         return _options_dict(o)
+
+
+def csf_workspace_bytes(order: int, nnz: int) -> int:
+    need = ctypes.c_size_t()
+    _check(lib().qsd_csf_workspace_bytes(int(order), int(nnz), ctypes.byref(need)),
+           "qsd_csf_workspace_bytes")
+    return max(int(need.value), 256)
+
+
+def csf_build(coords, sigma: Sequence[int], ids, ptr, nodes, workspace, stream=None) -> None:
+    """qsd_csf_build into preallocated int32 CUDA tensors: ids[l] (capacity
+    >= nnz), ptr[0] (2), ptr[l] (nnz + 1), nodes (r + 1)."""
+    r, nnz = int(coords.shape[0]), int(coords.shape[1])
+    out = _capi.Csf()
+    for l in range(r):
+        out.ids[l] = ids[l].data_ptr()
+    for l in range(r + 1):
+        out.ptr[l] = ptr[l].data_ptr()
+    stride = int(coords.stride(0)) if nnz else 0
+    _check(lib().qsd_csf_build(ctypes.c_void_p(coords.data_ptr()) if nnz else None, stride, nnz,
+                               r, _i32(sigma), ctypes.byref(out),
+                               ctypes.c_void_p(nodes.data_ptr()),
+                               ctypes.c_void_p(workspace.data_ptr()), int(workspace.numel()),
+                               _stream_handle(stream)), "qsd_csf_build")
+
+
+def csf_levels(coords, sigma: Sequence[int], stream=None):
+    """CSF levels (qsd_csf_build) of a tensor sorted under sigma.
+
+    coords: int32 CUDA tensor (r, nnz) sorted under sigma (for example
+    transpose()'s result for target order sigma). Returns (ids, ptr): ids[l]
+    holds level l+1's node ids, ptr[l] the first child of each level-l node
+    (l < r) or the first entry of each leaf (l == r), plus an end marker; all
+    int32 CUDA tensors sized to the node counts (read back with one sync).
+    """
+    import torch
+    r, nnz = int(coords.shape[0]), int(coords.shape[1])
+    dev = coords.device
+    cap = max(nnz, 1)
+    ids = [torch.empty(cap, dtype=torch.int32, device=dev) for _ in range(r)]
+    ptr = [torch.empty(2 if l == 0 else cap + 1, dtype=torch.int32, device=dev)
+           for l in range(r + 1)]
+    nodes = torch.empty(r + 1, dtype=torch.int32, device=dev)
+    ws = torch.empty(csf_workspace_bytes(r, nnz), dtype=torch.uint8, device=dev)
+    csf_build(coords, sigma, ids, ptr, nodes, ws, stream)
+    n = [int(x) for x in nodes.cpu()]  # synchronises with the stream's work
+    return ([ids[l][:n[l + 1]] for l in range(r)],
+            [ptr[l][:n[l] + 1] for l in range(r + 1)])
 
 
 def server_clock() -> float:

@@ -85,6 +85,10 @@ class ServerStats(ctypes.Structure):
                 ("bytes_in_use", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t)]
 
 
+class Csf(ctypes.Structure):
+    _fields_ = [("ids", ctypes.c_void_p * MAX_ORDER), ("ptr", ctypes.c_void_p * (MAX_ORDER + 1))]
+
+
 # (name, restype, argtypes) for every entry point of include/qsd.h
 P = ctypes.c_void_p
 I = ctypes.c_int
@@ -105,6 +109,8 @@ SIGNATURES = [
                                ctypes.POINTER(Values), P, ctypes.c_size_t, P]),
     ("qsd_workspace_status", I, [P, P, ctypes.POINTER(I)]),
     ("qsd_get_async_status", I, [P, ctypes.POINTER(I)]),
+    ("qsd_csf_workspace_bytes", I, [I, I64, ctypes.POINTER(ctypes.c_size_t)]),
+    ("qsd_csf_build", I, [P, I64, I64, I, P, ctypes.POINTER(Csf), P, P, ctypes.c_size_t, P]),
     ("qsd_batch_create", I, [ctypes.POINTER(BatchItem), I, I, ctypes.POINTER(BatchOptions),
                              ctypes.POINTER(P)]),
     ("qsd_batch_workspace_bytes", I, [P, ctypes.POINTER(ctypes.c_size_t)]),

@@ -174,6 +174,16 @@ cudaError_t launch_local_sort(const Cols& c, const PassList& pl,
                               int single, int nnz, int capacity,
                               unsigned* status, const LsBatch& lb, cudaStream_t stream);
 
+// CSF levels of a tensor sorted under sigma (rows given in sigma order).
+struct CsfOut {
+  int32_t* ids[kMaxOrder];      // level l + 1 node ids
+  int32_t* ptr[kMaxOrder + 1];  // level l: first child (l < order) / first entry (l == order)
+};
+cudaError_t launch_csf(const int32_t* const* rows_in_sigma_order, int order, int nnz,
+                       const CsfOut& out, int32_t* nodes, uint32_t* tile_count,
+                       cudaStream_t stream);
+size_t csf_workspace_bytes(int order, int nnz);
+
 // Copies every coordinate row and the values from c.in to c.out (entries
 // [0, nnz)): a zero-pass plan asked for a distinct output buffer.
 cudaError_t launch_copy(const Cols& c, int nnz, cudaStream_t stream);
