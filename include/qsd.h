@@ -97,7 +97,12 @@ typedef struct {
                             once: 1024, 2048, 3584 or 4096 (smaller when the
                             rows do not fit); 0 = automatic */
   int chunk_tiles;       /* tiles per chunk, the unit of the per-chunk digit
-                            counts, 1..256; 0 = automatic (8) */
+                            counts, 1..256; 0 = automatic (4) */
+  int global_groups;     /* nonzero: run every group that has a prefix as one
+                            global sort by (prefix, key) instead of sorting
+                            each bucket of equal prefix by the key (the same
+                            result: the group's input is sorted by its
+                            prefix); more digit passes, no bucket work */
 } qsd_plan_options;
 
 /* Description of a plan (qsd_plan_get_info). */
@@ -233,6 +238,25 @@ qsd_status qsd_workspace_status(const void* workspace, void* stream,
  * status word, which every transpose on that device ORs its errors into. */
 qsd_status qsd_get_async_status(void* stream, qsd_status* out);
 
+/* ---- Plan tuner ----
+ * The paper ranks plans by their number of partial sorts and leaves choosing
+ * by measured cost to future work. qsd_plan_tune does that for one tensor:
+ * starting from the plan's options it times out-of-place transpositions of
+ * the caller's data (qsd_transpose_from_ws, `reps` timed runs per candidate,
+ * CUDA events on `stream`) under one changed option at a time -- groups with
+ * a prefix as bucket sorts or as global sorts (global_groups), digit width,
+ * tile size, bucket capacity, chunk length -- keeps the fastest, and writes
+ * its options to *best (and its time per transposition to *best_ms, may be
+ * NULL). Every candidate gives the same result (the plan's calls are
+ * fixed). Candidates needing more than workspace_bytes are skipped;
+ * qsd_plan_tune_workspace_bytes gives an amount that fits all of them. The
+ * output buffers are overwritten. Synchronises `stream`. */
+qsd_status qsd_plan_tune_workspace_bytes(qsd_plan_t plan, int64_t nnz, size_t* bytes);
+qsd_status qsd_plan_tune(qsd_plan_t plan, const int32_t* in_coords, int64_t in_stride,
+                         const void* in_vals, qsd_coords* out_coords, qsd_values* out_vals,
+                         int64_t nnz, void* workspace, size_t workspace_bytes, void* stream,
+                         int reps, qsd_plan_options* best, float* best_ms);
+
 /* ---- Compressed sparse fiber levels ----
  * The CSF tree of Section 2.1 for a tensor sorted under sigma (for example a
  * result of qsd_transpose with target_perm sigma): level l (1..order) has one
@@ -300,7 +324,7 @@ typedef struct {
   int digit_bits;      /* 0 = each plan's own */
   int local_capacity;  /* 0 = 4096 */
   int tile;            /* 0 = automatic */
-  int chunk_tiles;     /* 0 = 8 */
+  int chunk_tiles;     /* 0 = 4 */
   int no_graph;        /* nonzero: launch directly instead of replaying a graph */
   int use_tuned;       /* nonzero: take the options the tuning cache holds for
                           a batch of this shape, if any (qsd_batch_tune) */

@@ -17,6 +17,7 @@ from typing import List, Optional, Sequence, Tuple
 from . import _capi
 
 __all__ = ["Plan", "QsdError", "Batch", "Server", "server_clock", "csf_levels", "csf_build",
+           "tune_plan",
            "csf_workspace_bytes", "transpose", "transpose_buffers", "transpose_from",
            "transpose_host", "transpose_noalloc", "tune_cache_save", "tune_cache_load",
            "get_async_status", "workspace_status", "build", "lib", "LIB_PATH"]
@@ -60,7 +61,7 @@ class Plan:
                  input_mode_order: Optional[Sequence[int]] = None, *,
                  validate: bool = False, digit_bits: int = 0,
                  local_capacity: int = 0, no_skip: bool = False, tile: int = 0,
-                 chunk_tiles: int = 0):
+                 chunk_tiles: int = 0, global_groups: bool = False):
         L = lib()
         r = len(dims)
         self.dims = [int(d) for d in dims]
@@ -69,10 +70,12 @@ class Plan:
         self.input_mode_order = list(range(r)) if input_mode_order is None else \
             [int(x) for x in input_mode_order]
         opts = _capi.PlanOptions(int(bool(validate)), int(digit_bits), int(local_capacity),
-                                 int(bool(no_skip)), int(tile), int(chunk_tiles))
+                                 int(bool(no_skip)), int(tile), int(chunk_tiles),
+                                 int(bool(global_groups)))
         self.options = dict(validate=bool(validate), digit_bits=int(digit_bits),
                             local_capacity=int(local_capacity), no_skip=bool(no_skip),
-                            tile=int(tile), chunk_tiles=int(chunk_tiles))
+                            tile=int(tile), chunk_tiles=int(chunk_tiles),
+                            global_groups=bool(global_groups))
         handle = ctypes.c_void_p()
         dims_arr = (ctypes.c_int64 * max(r, 1))(*self.dims)
         st = L.qsd_plan_ex(r, dims_arr, _i32(self.input_mode_order) if r else None,
@@ -299,6 +302,45 @@ class Batch:
                                         int(workspace.numel()), _stream_handle(stream),
                                         int(reps), ctypes.byref(o)), "qsd_batch_tune")
         return _options_dict(o)
+
+
+def tune_plan(plan: "Plan", in_coords, in_vals, reps: int = 3, stream=None):
+    """qsd_plan_tune: times the plan's equivalent variants on this tensor
+    (out of place; the input is not modified) and returns (tuned Plan, ms per
+    transposition, options dict)."""
+    import torch
+    nnz = int(in_coords.shape[1])
+    need = ctypes.c_size_t()
+    _check(lib().qsd_plan_tune_workspace_bytes(plan.handle, nnz, ctypes.byref(need)),
+           "qsd_plan_tune_workspace_bytes")
+    dev = in_coords.device
+    ws = torch.empty(max(int(need.value), 256), dtype=torch.uint8, device=dev)
+    cb = [torch.empty_like(in_coords) for _ in range(2)]
+    c = _capi.Coords()
+    c.buf[0], c.buf[1] = cb[0].data_ptr(), cb[1].data_ptr()
+    c.stride = int(in_coords.stride(0))
+    v = _capi.Values()
+    vb = None
+    if in_vals is not None:
+        vb = [torch.empty_like(in_vals) for _ in range(2)]
+        v.buf[0], v.buf[1] = vb[0].data_ptr(), vb[1].data_ptr()
+        v.elem_bytes = _val_bytes(in_vals)
+    best = _capi.PlanOptions()
+    ms = ctypes.c_float()
+    _check(lib().qsd_plan_tune(plan.handle, ctypes.c_void_p(in_coords.data_ptr()),
+                               int(in_coords.stride(0)),
+                               ctypes.c_void_p(in_vals.data_ptr()) if in_vals is not None else None,
+                               ctypes.byref(c), ctypes.byref(v), nnz,
+                               ctypes.c_void_p(ws.data_ptr()), int(ws.numel()),
+                               _stream_handle(stream), int(reps), ctypes.byref(best),
+                               ctypes.byref(ms)), "qsd_plan_tune")
+    opts = {k: int(getattr(best, k)) for k, _ in _capi.PlanOptions._fields_}
+    tuned = Plan(plan.dims, plan.target_perm, plan.input_mode_order,
+                 validate=bool(opts["validate"]), digit_bits=opts["digit_bits"],
+                 local_capacity=opts["local_capacity"], no_skip=bool(opts["no_skip"]),
+                 tile=opts["tile"], chunk_tiles=opts["chunk_tiles"],
+                 global_groups=bool(opts["global_groups"]))
+    return tuned, float(ms.value), opts
 
 
 def csf_workspace_bytes(order: int, nnz: int) -> int:

@@ -28,7 +28,8 @@ class Values(ctypes.Structure):
 class PlanOptions(ctypes.Structure):
     _fields_ = [("validate", ctypes.c_int), ("digit_bits", ctypes.c_int),
                 ("local_capacity", ctypes.c_int), ("no_skip", ctypes.c_int),
-                ("tile", ctypes.c_int), ("chunk_tiles", ctypes.c_int)]
+                ("tile", ctypes.c_int), ("chunk_tiles", ctypes.c_int),
+                ("global_groups", ctypes.c_int)]
 
 
 _A = ctypes.c_int * MAX_ORDER
@@ -109,6 +110,10 @@ SIGNATURES = [
                                ctypes.POINTER(Values), P, ctypes.c_size_t, P]),
     ("qsd_workspace_status", I, [P, P, ctypes.POINTER(I)]),
     ("qsd_get_async_status", I, [P, ctypes.POINTER(I)]),
+    ("qsd_plan_tune_workspace_bytes", I, [P, I64, ctypes.POINTER(ctypes.c_size_t)]),
+    ("qsd_plan_tune", I, [P, P, I64, P, ctypes.POINTER(Coords), ctypes.POINTER(Values), I64, P,
+                          ctypes.c_size_t, P, I, ctypes.POINTER(PlanOptions),
+                          ctypes.POINTER(ctypes.c_float)]),
     ("qsd_csf_workspace_bytes", I, [I, I64, ctypes.POINTER(ctypes.c_size_t)]),
     ("qsd_csf_build", I, [P, I64, I64, I, P, ctypes.POINTER(Csf), P, P, ctypes.c_size_t, P]),
     ("qsd_batch_create", I, [ctypes.POINTER(BatchItem), I, I, ctypes.POINTER(BatchOptions),

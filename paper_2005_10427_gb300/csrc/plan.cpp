@@ -157,6 +157,23 @@ qsd_status qsd_plan_ex(int order, const int64_t* dims,
       }
       l = l_next;
     }
+    if (o.global_groups) {
+      // An equivalent execution: the input of a group is already sorted by
+      // its prefix, so one stable sort of the whole tensor by (prefix, key)
+      // gives what sorting every bucket by the key gives -- with more digit
+      // passes but no bucket discovery or bucket sort.
+      for (int gi = 0; gi < p->ngroups; ++gi) {
+        qsd::Group& g = p->groups[gi];
+        if (g.prefix_len == 0) continue;
+        int keys[QSD_MAX_ORDER];
+        int nk = 0;
+        for (int i = 0; i < g.prefix_len; ++i) keys[nk++] = g.prefix_modes[i];
+        for (int i = 0; i < g.nkeys; ++i) keys[nk++] = g.key_modes[i];
+        g.nkeys = nk;
+        for (int i = 0; i < nk; ++i) g.key_modes[i] = keys[i];
+        g.prefix_len = 0;
+      }
+    }
   }
   for (int i = 0; i < p->ngroups; ++i)
     schedule_digits(p->dims, p->groups[i], p->digit_bits);

@@ -160,6 +160,33 @@ def test_tile_sizes_and_chunk_lengths(qsd, tile, chunk_tiles):
         check(qsd, coords, vals, dims, sigma, tile=tile, chunk_tiles=chunk_tiles)
 
 
+@pytest.mark.parametrize("r", [3, 4])
+def test_global_groups_give_the_same_result(qsd, r):
+    # groups with a prefix run as global sorts by (prefix, key)
+    dims = [30, 200, 50, 7][:r]
+    coords, vals = tensor(dims, 60_000, seed=70 + r, zipf=1.2, dup=0.05)
+    for sigma in itertools.permutations(range(r)):
+        check(qsd, coords, vals, dims, sigma, global_groups=True)
+
+
+def test_plan_tuner_result_and_options(qsd):
+    dims = [300, 2000, 3000]
+    coords, vals = tensor(dims, 300_000, seed=81, zipf=1.1)
+    sigma = (0, 2, 1)
+    plan = qsd.Plan(dims, sigma)
+    c = torch.from_numpy(coords).cuda()
+    v = torch.from_numpy(vals).cuda()
+    tuned, ms, opts = qsd.tune_plan(plan, c, v, reps=1)
+    assert ms > 0
+    assert opts["digit_bits"] in (5, 6, 7, 8) and opts["tile"] in (0, 2048, 3584, 4096)
+    assert opts["global_groups"] in (0, 1) and opts["chunk_tiles"] in (2, 4, 8)
+    assert torch.equal(c.cpu(), torch.from_numpy(coords))  # the input is left alone
+    gc, gv = qsd.transpose(c.clone(), v.clone(), tuned)
+    rc, rv = oracle.transpose(coords, vals, sigma)
+    assert np.array_equal(gc.cpu().numpy(), rc)
+    assert np.array_equal(gv.cpu().numpy().view(np.uint32), rv.view(np.uint32))
+
+
 @pytest.mark.parametrize("cap", [1024, 2048, 4096, 8192])
 def test_local_capacities(qsd, cap):
     dims = [3000, 500, 700]
