@@ -155,6 +155,33 @@ def cpu_oracle_rate(t_coords: np.ndarray, t_vals: np.ndarray, perms, target_s=15
                       f"core, {dt:.1f} s"}
 
 
+def cpu_method_rate(t_coords: np.ndarray, t_vals: np.ndarray, dims, perms, target_s=8.0):
+    """The paper's own CPU method (Algorithms 1-3 as counting sorts, parallel
+    as its Section 3.2 describes; OpenMP on all host cores) on a strided
+    sample of the workload, sized to about target_s seconds."""
+    import oracle
+    n_total = t_coords.shape[1]
+    threads = oracle.cpu_method_threads()
+
+    def run(m):
+        idx = np.linspace(0, n_total - 1, m).astype(np.int64)
+        c, v = np.ascontiguousarray(t_coords[:, idx]), np.ascontiguousarray(t_vals[idx])
+        t0 = time.perf_counter()
+        for sigma in perms:
+            oracle.cpu_method_transpose(c, v, dims, sigma)
+        return time.perf_counter() - t0
+
+    m = min(n_total, 1_000_000)
+    dt = run(m)
+    while m < n_total and dt < 0.4 * target_s:
+        m = int(min(n_total, m * min(4.0, 0.8 * target_s / max(dt, 1e-3))))
+        dt = run(m)
+    return {"value": len(perms) * m / dt / 1e9, "unit": "Gnnz/s", "cores": threads,
+            "kind": "paper's CPU method (Algorithms 1-3 as parallel counting sorts)",
+            "sample": f"{m} entries (every {n_total / m:.1f}-th of the workload), all "
+                      f"{len(perms)} target orders, {threads} host threads, {dt:.1f} s"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -187,6 +214,8 @@ def run_reference(args, rank, world):
                                        f"per step"},
             "e2e": {"value": value, "unit": "Gnnz/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+    if not args.no_cpu_baseline:
+        line["cpu_method"] = cpu_method_rate(coords, vals, wl["dims"], perms)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -355,9 +384,11 @@ def main():
     if args.check:
         check = sampled_check(qsd, t, plans, perms, cb, vbuf, ws, stream)
 
-    cpu = None
+    cpu = cpu_method = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_rate(t.coords.cpu().numpy(), t.vals.cpu().numpy(), perms)
+        hc, hv = t.coords.cpu().numpy(), t.vals.cpu().numpy()
+        cpu = cpu_oracle_rate(hc, hv, perms)
+        cpu_method = cpu_method_rate(hc, hv, wl["dims"], perms)
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": "Gnnz/s", "n_gpus": world,
@@ -377,6 +408,8 @@ def main():
                                 "share": round(a["ms"] / total_ms, 4) if total_ms else None}
                             for k, a in sorted(agg.items(), key=lambda kv: -kv[1]["ms"])},
                 "clocks": clocks}
+        if cpu_method is not None:
+            line["cpu_method"] = cpu_method
         if csf is not None:
             line["csf"] = csf
         if batched is not None:

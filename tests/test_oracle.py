@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 import oracle
+import synth
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -164,3 +165,29 @@ def test_rank_under_matches_the_stable_sort():
         # the first entry of each run of equal coordinates sits exactly at `less`
         less, equal = oracle.rank_under(coords, sigma, out[:, 0])
         assert less == 0 and equal >= 1
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 4, 5])
+def test_cpu_method_equals_oracle(r):
+    # the paper's method restated on the host (Algorithms 1-3 as parallel
+    # counting sorts) gives the definition's result for every order
+    dims = [13, 7, 29, 5, 3][:r]
+    t = synth.random_coo(dims, 2500, seed=90 + r, dup_frac=0.2, zipf=1.1)
+    c, v = t.coords.numpy(), t.vals.numpy()
+    for sigma in itertools.permutations(range(r)):
+        a = oracle.transpose(c, v, sigma)
+        for threads in (1, 3):
+            b = oracle.cpu_method_transpose(c, v, dims, sigma, threads=threads)
+            assert np.array_equal(a[0], b[0]), (sigma, threads)
+            assert np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
+
+
+def test_cpu_method_non_identity_input_order():
+    dims = [20, 30, 10, 6]
+    tau = (2, 0, 3, 1)
+    t = synth.random_coo(dims, 4000, seed=99, dup_frac=0.1, input_order=tau)
+    c, v = t.coords.numpy(), t.vals.numpy()
+    for sigma in itertools.permutations(range(4)):
+        a = oracle.transpose(c, v, sigma)
+        b = oracle.cpu_method_transpose(c, v, dims, sigma, tau=tau)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), sigma
