@@ -129,6 +129,22 @@ def committed_traffic(kernel: str, workload: str):
     return d.get(workload, {}).get(kernel)
 
 
+def combine_ranks(ms: float, world: int, device) -> float:
+    """The timed region's duration for the whole job: the slowest rank's
+    (max over ranks; every rank gets it)."""
+    if world <= 1:
+        return ms
+    tt = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def aggregate_value(world: int, entries_per_step: int, steps: int, ms: float) -> float:
+    """Whole-job throughput (Gnnz/s): the entries all ranks transposed over the
+    slowest rank's time (the replicas each run the full per-GPU workload)."""
+    return world * entries_per_step * steps / (ms / 1e3) / 1e9
+
+
 def cpu_oracle_rate(t_coords: np.ndarray, t_vals: np.ndarray, perms, target_s=15.0):
     """The oracle (single-threaded std::stable_sort) on a strided sample of the
     workload (every k-th entry: still sorted in the input order, with the
@@ -299,15 +315,12 @@ def main():
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
+    ms = combine_ranks(ev0.elapsed_time(ev1), world, dev)
     if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
         torch.distributed.barrier()
     ms_per_step = ms / args.steps
     entries_per_step = len(perms) * nnz
-    value = world * entries_per_step * args.steps / (ms / 1e3) / 1e9
+    value = aggregate_value(world, entries_per_step, args.steps, ms)
 
     # Live per-kernel timings over the same steps (instrumented replay).
     qsd.profile_reset()
