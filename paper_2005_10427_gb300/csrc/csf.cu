@@ -26,70 +26,82 @@ namespace {
 
 constexpr int kCsfThreads = 256;
 constexpr int kCsfWarps = kCsfThreads / 32;
-constexpr int kCsfItems = 16;
+constexpr int kCsfItems = 16;  // consecutive entries per thread
 constexpr int kCsfTile = kCsfThreads * kCsfItems;
 
 struct CsfIn {
   const int32_t* col[kMaxOrder];  // the rows in sigma order: col[l] = row sigma_l
   int order;
   int nnz;
+  int vec;  // every row 16-byte aligned: 16-byte loads
 };
 
-// L(j) for the entries of a warp's rounds: lane l of round i holds entry
-// base + 32 i + l. prev[] carries the previous round's last entry.
-struct LevelScan {
-  int32_t prev[kMaxOrder];
-};
-
-__device__ __forceinline__ int first_level(const CsfIn& in, int j, int lane, int32_t (&v)[kMaxOrder],
-                                           LevelScan& ls, bool first_in_warp) {
-  int L = in.order + 1;
-  const bool ok = j < in.nnz;
+// The 16 values of row l at entries j0 .. j0 + 15 (j0 a multiple of 16), and
+// the value of entry j0 - 1. Entries past the end read as 0.
+__device__ __forceinline__ void load_run(const CsfIn& in, int l, int j0, uint32_t (&v)[kCsfItems],
+                                         uint32_t& before) {
+  const int32_t* row = in.col[l];
+  before = j0 > 0 && j0 - 1 < in.nnz ? (uint32_t)__ldg(row + j0 - 1) : 0u;
+  if (in.vec && j0 + kCsfItems <= in.nnz) {
+    const uint4* r4 = reinterpret_cast<const uint4*>(row + j0);
 #pragma unroll
-  for (int l = 0; l < kMaxOrder; ++l) {  // unrolled to the largest order: registers only
-    if (l < in.order) {
-      v[l] = ok ? __ldg(in.col[l] + j) : 0;
-      int32_t p = __shfl_up_sync(0xffffffffu, v[l], 1);
-      const int32_t last = __shfl_sync(0xffffffffu, v[l], 31);
-      if (lane == 0) p = ls.prev[l];
-      ls.prev[l] = last;
-      if (L > in.order && (j == 0 || v[l] != p)) L = l + 1;
+    for (int q = 0; q < kCsfItems / 4; ++q) {
+      const uint4 x = __ldg(r4 + q);
+      v[4 * q] = x.x;
+      v[4 * q + 1] = x.y;
+      v[4 * q + 2] = x.z;
+      v[4 * q + 3] = x.w;
     }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kCsfItems; ++k)
+      v[k] = j0 + k < in.nnz ? (uint32_t)__ldg(row + j0 + k) : 0u;
   }
-  (void)first_in_warp;
-  return ok ? L : in.order + 2;  // past the end: no node on any level
 }
 
-__device__ __forceinline__ void load_prev(const CsfIn& in, int base, int lane, LevelScan& ls) {
+// L(j) of the thread's 16 entries (4 bits each): the first level (1-based)
+// whose mode differs from the entry before (1 at entry 0, order + 1 for a
+// duplicate, order + 2 past the end). Reads the rows level by level.
+__device__ __forceinline__ void first_levels(const CsfIn& in, int j0, uint32_t (&L)[2]) {
+  uint32_t lv[kCsfItems];
 #pragma unroll
-  for (int l = 0; l < kMaxOrder; ++l) {
-    const int jp = base - 1;
-    ls.prev[l] = (l < in.order && lane == 0 && jp >= 0 && jp < in.nnz) ? __ldg(in.col[l] + jp) : 0;
+  for (int k = 0; k < kCsfItems; ++k)
+    lv[k] = j0 + k >= in.nnz ? in.order + 2 : (j0 + k == 0 ? 1 : in.order + 1);
+#pragma unroll 1
+  for (int l = 0; l < in.order; ++l) {
+    uint32_t v[kCsfItems], before;
+    load_run(in, l, j0, v, before);
+#pragma unroll
+    for (int k = 0; k < kCsfItems; ++k) {
+      const uint32_t prev = k ? v[k - 1] : before;
+      if (lv[k] == (uint32_t)in.order + 1 && v[k] != prev) lv[k] = l + 1;
+    }
   }
+  L[0] = L[1] = 0;
+#pragma unroll
+  for (int k = 0; k < kCsfItems; ++k) L[k / 8] |= lv[k] << ((k % 8) * 4);
+}
+
+__device__ __forceinline__ uint32_t level_of(const uint32_t (&L)[2], int k) {
+  return (L[k / 8] >> ((k % 8) * 4)) & 15u;
 }
 
 __global__ void __launch_bounds__(kCsfThreads)
-k_csf_count(CsfIn in, uint32_t* __restrict__ tile_count, int ntiles) {
+k_csf_count(const __grid_constant__ CsfIn in, uint32_t* __restrict__ tile_count, int ntiles) {
   __shared__ uint32_t s_cnt[kCsfWarps][kMaxOrder];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, t = blockIdx.x;
-  const int base = t * kCsfTile + w * kCsfItems * 32;
-  LevelScan ls;
-  load_prev(in, base, lane, ls);
-  uint32_t cnt[kMaxOrder];
+  const int j0 = t * kCsfTile + threadIdx.x * kCsfItems;
+  uint32_t L[2];
+  first_levels(in, j0, L);
 #pragma unroll
-  for (int l = 0; l < kMaxOrder; ++l) cnt[l] = 0;
-#pragma unroll 4
-  for (int i = 0; i < kCsfItems; ++i) {
-    int32_t v[kMaxOrder];
-    const int L = first_level(in, base + i * 32 + lane, lane, v, ls, i == 0);
+  for (int l = 0; l < kMaxOrder; ++l) {
+    if (l >= in.order) break;
+    uint32_t c = 0;
 #pragma unroll
-    for (int l = 0; l < kMaxOrder; ++l)
-      if (l < in.order) cnt[l] += __popc(__ballot_sync(0xffffffffu, L <= l + 1));
-  }
-  if (lane == 0) {
+    for (int k = 0; k < kCsfItems; ++k) c += level_of(L, k) <= (uint32_t)l + 1 ? 1u : 0u;
 #pragma unroll
-    for (int l = 0; l < kMaxOrder; ++l)
-      if (l < in.order) s_cnt[w][l] = cnt[l];
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) s_cnt[w][l] = c;
   }
   __syncthreads();
   if (threadIdx.x < in.order) {
@@ -139,63 +151,40 @@ k_csf_scan(uint32_t* __restrict__ tile_count, int ntiles, int order, int nnz, Cs
 }
 
 __global__ void __launch_bounds__(kCsfThreads)
-k_csf_write(CsfIn in, const uint32_t* __restrict__ tile_off, int ntiles, CsfOut out) {
-  __shared__ uint32_t s_cnt[kCsfWarps][kMaxOrder];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, t = blockIdx.x;
-  const int base = t * kCsfTile + w * kCsfItems * 32;
-  const uint32_t lt = (1u << lane) - 1u;
-  // first sweep: L of every item (4 bits each), the warp's count per level
-  LevelScan ls;
-  load_prev(in, base, lane, ls);
-  uint32_t Lp[kCsfItems / 8] = {0u, 0u};
-  uint32_t cnt[kMaxOrder];
+k_csf_write(const __grid_constant__ CsfIn in, const uint32_t* __restrict__ tile_off, int ntiles,
+            const __grid_constant__ CsfOut out) {
+  __shared__ uint32_t s_tmp[kCsfWarps + 1];
+  const int t = blockIdx.x;
+  const int j0 = t * kCsfTile + threadIdx.x * kCsfItems;
+  uint32_t L[2];
+  first_levels(in, j0, L);
+  // node index of each entry on the level above (valid where the entry starts
+  // a node there)
+  uint32_t above[kCsfItems];
 #pragma unroll
-  for (int l = 0; l < kMaxOrder; ++l) cnt[l] = 0;
+  for (int k = 0; k < kCsfItems; ++k) above[k] = 0;
+#pragma unroll 1
+  for (int l = 0; l < in.order; ++l) {
+    // the thread's first node index on level l + 1
+    uint32_t c = 0;
 #pragma unroll
-  for (int i = 0; i < kCsfItems; ++i) {
-    int32_t v[kMaxOrder];
-    const int L = first_level(in, base + i * 32 + lane, lane, v, ls, i == 0);
-    Lp[i / 8] |= (uint32_t)L << ((i % 8) * 4);
+    for (int k = 0; k < kCsfItems; ++k) c += level_of(L, k) <= (uint32_t)l + 1 ? 1u : 0u;
+    uint32_t total;
+    uint32_t p = tile_off[(size_t)l * ntiles + t] + block_exclusive_sum<kCsfWarps>(c, s_tmp, &total);
+    uint32_t v[kCsfItems], before;
+    load_run(in, l, j0, v, before);
 #pragma unroll
-    for (int l = 0; l < kMaxOrder; ++l)
-      if (l < in.order) cnt[l] += __popc(__ballot_sync(0xffffffffu, L <= l + 1));
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int l = 0; l < kMaxOrder; ++l)
-      if (l < in.order) s_cnt[w][l] = cnt[l];
-  }
-  __syncthreads();
-  // the warp's first node index per level: the tile's, plus earlier warps'
-  uint32_t run[kMaxOrder];
-#pragma unroll
-  for (int l = 0; l < kMaxOrder; ++l) {
-    run[l] = 0;
-    if (l < in.order) {
-      run[l] = tile_off[(size_t)l * ntiles + t];
-      for (int k = 0; k < w; ++k) run[l] += s_cnt[k][l];
-    }
-  }
-  // second sweep: node indices and the writes
-#pragma unroll
-  for (int i = 0; i < kCsfItems; ++i) {
-    const int j = base + i * 32 + lane;
-    const int L = (int)((Lp[i / 8] >> ((i % 8) * 4)) & 15u);
-    uint32_t pprev = 0;
-#pragma unroll
-    for (int l = 0; l < kMaxOrder; ++l) {
-      if (l >= in.order) break;
-      const bool starts = L <= l + 1;  // j starts a node on level l + 1
-      const uint32_t bal = __ballot_sync(0xffffffffu, starts);
-      const uint32_t p = run[l] + __popc(bal & lt);
-      run[l] += __popc(bal);
-      if (starts) {
-        out.ids[l][p] = __ldg(in.col[l] + j);
-        if (L <= l) out.ptr[l][pprev] = (int32_t)p;  // j also started the parent
-        if (l == in.order - 1) out.ptr[in.order][p] = j;
+    for (int k = 0; k < kCsfItems; ++k) {
+      const uint32_t lk = level_of(L, k);
+      if (lk <= (uint32_t)l + 1) {  // entry j0 + k starts a node on level l + 1
+        out.ids[l][p] = (int32_t)v[k];
+        if (lk <= (uint32_t)l) out.ptr[l][above[k]] = (int32_t)p;  // and its parent
+        if (l == in.order - 1) out.ptr[in.order][p] = j0 + k;
+        above[k] = p;
+        ++p;
       }
-      pprev = p;
     }
+    __syncthreads();  // s_tmp is reused by the next level's scan
   }
 }
 
@@ -207,7 +196,11 @@ cudaError_t launch_csf(const int32_t* const* rows_in_sigma_order, int order, int
   CsfIn in;
   in.order = order;
   in.nnz = nnz;
-  for (int l = 0; l < kMaxOrder; ++l) in.col[l] = l < order ? rows_in_sigma_order[l] : nullptr;
+  in.vec = 1;
+  for (int l = 0; l < kMaxOrder; ++l) {
+    in.col[l] = l < order ? rows_in_sigma_order[l] : nullptr;
+    if (l < order && (reinterpret_cast<uintptr_t>(in.col[l]) & 15)) in.vec = 0;
+  }
   const int ntiles = (nnz + kCsfTile - 1) / kCsfTile;
   if (ntiles > 0) k_csf_count<<<ntiles, kCsfThreads, 0, stream>>>(in, tile_count, ntiles);
   k_csf_scan<<<1, 1024, 0, stream>>>(tile_count, ntiles, order, nnz, out, nodes);
