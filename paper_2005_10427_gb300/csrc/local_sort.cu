@@ -2,9 +2,10 @@
 //
 // Section 3.2 parallelises the bucketed sort by bucket boundaries: entries
 // never leave their bucket, so each processor sorts the buckets that begin
-// in its region. Here each thread block owns a window of `CAP` entries and
-// sorts the small buckets (at most CAP entries each) that begin in it, in
-// batches of consecutive buckets that fit shared memory together. A batch's
+// in its region. Here each thread block owns a window of a few times `CAP`
+// entries and sorts the small buckets (at most CAP entries each) that begin
+// in it, in batches of consecutive buckets that fit shared memory together
+// (a batch of tiny buckets is ranked by counting instead of the passes). A batch's
 // rows are staged in shared memory by bulk asynchronous copies (unaligned
 // edges by plain loads) while the block numbers the batch's buckets; the
 // batch is then stably sorted by (bucket, key): least-significant-digit-first
@@ -27,6 +28,8 @@ namespace {
 
 constexpr int kLsThreads = 512;
 constexpr int kLsWarps = kLsThreads / 32;
+constexpr int kTiny = 64;  // largest bucket of the rank-by-counting path
+constexpr int kLsSpan = 4;  // windows of CAP entries per block
 
 template <int VB>
 struct LsVal {
@@ -61,21 +64,28 @@ size_t ls_smem(int order, int vbytes) {
          (vbytes ? (size_t)CAP * vbytes + 16 : 0);
 }
 
-// First index i in [lo, hi) with a[i] > x (or hi).
-__device__ __forceinline__ int upper_bound_i(const int* a, int lo, int hi, int x) {
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (a[mid] <= x) lo = mid + 1; else hi = mid;
+// Search of a sorted array by a whole warp: the first index i in [lo, hi)
+// with a[i] > x (UPPER) or a[i] >= x (else), or hi. Each round probes 32
+// evenly spaced positions and keeps the gap between the last probe below x
+// and the first above, so a range of n takes about log32(n) dependent loads
+// (a binary search by one thread takes log2(n)). Every lane gets the result.
+template <bool UPPER>
+__device__ __forceinline__ int warp_search(const int* a, int lo, int hi, int x, int lane) {
+  while (hi - lo > 32) {
+    const int step = (hi - lo + 31) >> 5;
+    const int p = lo + lane * step;
+    const bool past = p >= hi || (UPPER ? __ldg(a + p) > x : __ldg(a + p) >= x);
+    const unsigned m = __ballot_sync(0xffffffffu, past);
+    const int f = m ? __ffs(m) - 1 : 32;
+    if (f == 0) return lo;
+    const int nlo = lo + (f - 1) * step + 1;
+    if (f < 32) hi = min(hi, lo + f * step);
+    lo = nlo;
   }
-  return lo;
-}
-// First index i in [lo, hi) with a[i] >= x (or hi).
-__device__ __forceinline__ int lower_bound_i(const int* a, int lo, int hi, int x) {
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (a[mid] < x) lo = mid + 1; else hi = mid;
-  }
-  return lo;
+  const int p = lo + lane;
+  const bool past = p < hi && (UPPER ? __ldg(a + p) > x : __ldg(a + p) >= x);
+  const unsigned m = __ballot_sync(0xffffffffu, past);
+  return m ? lo + __ffs(m) - 1 : hi;
 }
 
 template <int CAP, int VB>
@@ -90,51 +100,64 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
   uint8_t* stage = smem + ((sizeof(LsShared<CAP>) + 15) & ~size_t(15));
   uint8_t* const vstage = stage + (size_t)lay_order * kRow4;  // the value row
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int win0 = blockIdx.x * CAP;
-  if (win0 >= nnz) return;
-  const int win1 = min(win0 + CAP, nnz);
+  const int64_t w0 = (int64_t)blockIdx.x * CAP * kLsSpan;
+  if (w0 >= nnz) return;
+  const int win0 = (int)w0;
+  const int64_t w1 = w0 + (int64_t)CAP * kLsSpan;
+  const int win1 = w1 < nnz ? (int)w1 : nnz;
   const int nseg = single ? 1 : counters[kCntNumSeg];
 
-  if (threadIdx.x == 0) {
-    mbar_init(&S.ld, 1);
-    S.c = c1;
-    S.passes = pl.pass;
-    S.npasses = pl.npasses;
-    if (single) {
-      S.first = 0;
-      S.last = 1;
-    } else {
-      S.first = lower_bound_i(seg_start, 0, nseg, win0);
-      S.last = lower_bound_i(seg_start, S.first, nseg, win1);
+  // Warp 0 plans: the buckets that begin in the window are [first, last)
+  // (bucket starts are distinct, so at most win1 - win0 of them).
+  if (w == 0) {
+    int first = 0, last = 1;
+    if (!single) {
+      first = warp_search<false>(seg_start, 0, nseg, win0, lane);
+      last = warp_search<false>(seg_start, first, min(nseg, first + (win1 - win0) + 1), win1, lane);
+    }
+    if (lane == 0) {
+      mbar_init(&S.ld, 1);
+      S.c = c1;
+      S.passes = pl.pass;
+      S.npasses = pl.npasses;
+      S.first = first;
+      S.last = last;
     }
   }
   __syncthreads();
   const int last = S.last;
   int s = S.first;
   unsigned phase = 0;
+  // warp 0's view of the current tensor of a batch round: its index, where
+  // the next tensor starts, and the first bucket of the next tensor
+  int kt = -1, kt_end = 0, kt_seg = last;
   while (s < last) {
-    if (threadIdx.x == 0) {
-      const int a = single ? 0 : seg_start[s];
-      const int b = single ? nnz : seg_start[s + 1];
-      int e;
+    if (w == 0) {
+      const int a = single ? 0 : __ldg(seg_start + s);
+      const int b = single ? nnz : __ldg(seg_start + s + 1);
       int lim = last;
       if (lb.n > 0) {  // the bucket's tensor; the batch ends where the next one starts
-        const int k = upper_bound_i(lb.jbase, 0, lb.n + 1, a) - 1;
-        S.c = lb.t[k].c;
-        S.passes = lb.t[k].pass;
-        S.npasses = lb.t[k].npasses;
-        const int tb = lower_bound_i(seg_start, s + 1, nseg + 1, lb.jbase[k + 1]);
-        if (tb < lim) lim = tb;
+        if (kt < 0 || a >= kt_end) {
+          kt = warp_search<true>(lb.jbase, 0, lb.n + 1, a, lane) - 1;
+          kt_end = __ldg(lb.jbase + kt + 1);
+          kt_seg = warp_search<false>(seg_start, s + 1, last + 1, kt_end, lane);
+          if (lane == 0) {
+            S.c = lb.t[kt].c;
+            S.passes = lb.t[kt].pass;
+            S.npasses = lb.t[kt].npasses;
+          }
+        }
+        lim = min(lim, kt_seg);
       }
+      int e;
       if (b - a > CAP) {
         e = -1;  // large bucket: sorted by the digit passes
       } else if (single) {
         e = 1;
-      } else {
-        e = upper_bound_i(seg_start, s + 1, nseg + 1, a + CAP) - 1;
-        if (e > lim) e = lim;
+      } else {  // the most buckets from s whose entries fit CAP, within the tensor
+        e = min(warp_search<true>(seg_start, s + 1, lim + 1, a + CAP, lane) - 1, lim);
       }
-      S.batch_end = e;
+      if (lane == 0) S.batch_end = e;
     }
     __syncthreads();
     const int e = S.batch_end;
@@ -189,6 +212,18 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
       }
     }
 
+    // Batches of tiny buckets (at most kTiny entries, typical where the prefix
+    // is nearly unique) whose packed key fits the scratch are ranked by
+    // counting inside each bucket (below); the others by radix passes.
+    constexpr int kScratchWords = kLsWarps * kRadix;  // the ranking counters' space
+    constexpr int kKeyBits = CAP * 2 <= kScratchWords ? 64 : CAP <= kScratchWords ? 32 : 0;
+    int key_bits = 0;
+    for (int p = 0; p < S.npasses; ++p) key_bits += S.passes[p].bits;
+    bool small = kKeyBits > 0 && !single && key_bits <= kKeyBits;
+    for (int k = s + threadIdx.x; k < e && small; k += kLsThreads)
+      small = seg_start[k + 1] - seg_start[k] <= kTiny;
+    const bool tiny = __syncthreads_and(small);
+
     // Bucket index of every batch position (marks at bucket starts, scanned),
     // while the rows load.
     if (nsb > 1) {
@@ -235,7 +270,48 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
     int seg_bits = 0;
     while ((1 << seg_bits) < nsb) ++seg_bits;
     const int seg_passes = (seg_bits + kRadixBits - 1) / kRadixBits;
-    for (int p = 0; p < key_passes + seg_passes; ++p) {
+    if (kKeyBits > 0 && tiny) {
+      // Rank by counting: an entry's place in its bucket is the number of the
+      // bucket's entries with a smaller packed key, or an equal key earlier in
+      // the bucket (stable). Packed keys (the key passes' digits, least
+      // significant first) are built once into the counters' space.
+      uint64_t* key64 = reinterpret_cast<uint64_t*>(S.warp_hist);
+      uint32_t* key32 = S.warp_hist;
+      const bool k64 = kKeyBits == 64 && key_bits > 32;
+      for (int i = threadIdx.x; i < n; i += kLsThreads) {
+        uint64_t key = 0;
+        int off = 0;
+#pragma unroll 1
+        for (int p = 0; p < key_passes; ++p) {
+          const PassDesc& pd = passes[p];
+          uint32_t d = 0;
+          for (int k = 0; k < pd.nfields; ++k) {
+            const DigitField f = pd.f[k];
+            const uint32_t* row =
+                reinterpret_cast<const uint32_t*>(row_smem(f.mode) + S.row_off[f.mode]);
+            d |= field_bits(row[i], f);
+          }
+          key |= (uint64_t)d << off;
+          off += pd.bits;
+        }
+        if (k64) key64[i] = key; else key32[i] = (uint32_t)key;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += kLsThreads) {
+        const int b = nsb > 1 ? S.segid[i] : 0;
+        const int a = seg_start[s + b] - A, z = seg_start[s + b + 1] - A;
+        const uint64_t ki = k64 ? key64[i] : key32[i];
+        int r = a;
+#pragma unroll 1
+        for (int y = a; y < z; ++y) {
+          const uint64_t ky = k64 ? key64[y] : key32[y];
+          r += (ky < ki || (ky == ki && y < i)) ? 1 : 0;
+        }
+        S.perm[0][r] = (uint16_t)i;
+      }
+      __syncthreads();
+    }
+    for (int p = 0; p < (tiny ? 0 : key_passes + seg_passes); ++p) {
       uint32_t dig[ITEMS], rank[ITEMS], el[ITEMS];
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) {
@@ -293,7 +369,7 @@ cudaError_t launch_ls(const Cols& c, const PassList& pl, const int* seg_start,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  const int grid = single ? 1 : (nnz + CAP - 1) / CAP;
+  const int grid = single ? 1 : (int)(((int64_t)nnz + (int64_t)CAP * kLsSpan - 1) / ((int64_t)CAP * kLsSpan));
   if (grid < 1) return cudaSuccess;
   k_local_sort<CAP, VB><<<grid, kLsThreads, smem, stream>>>(c, pl, seg_start, counters,
                                                             single, nnz, lb, c.order, status);

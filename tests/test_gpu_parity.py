@@ -195,6 +195,22 @@ def test_local_capacities(qsd, cap):
         check(qsd, coords, vals, dims, sigma, local_capacity=cap)
 
 
+@pytest.mark.parametrize("cap", [1024, 2048, 4096])
+def test_tiny_buckets_ranked_by_counting(qsd, cap):
+    # Zipf prefix coordinates: a few large buckets (the radix passes or the
+    # digit passes), then thousands of buckets of a few entries, whose batches
+    # are ranked by counting; packed keys of 36 bits (64-bit counting keys up
+    # to capacity 2048, the radix passes above), of 4 bits with many equal
+    # keys inside a bucket, and of 24 bits; duplicate coordinates keep their
+    # input order.
+    cases = [([20000, 4, 1 << 18, 1 << 18], (0, 3, 2, 1)),
+             ([20000, 50, 3, 3], (0, 3, 2, 1)),
+             ([30000, 1 << 12, 1 << 12, 7], (0, 2, 1, 3))]
+    for i, (dims, sigma) in enumerate(cases):
+        coords, vals = tensor(dims, 150_000, seed=90 + i, zipf=0.9, dup=0.2)
+        check(qsd, coords, vals, dims, sigma, local_capacity=cap)
+
+
 def test_no_skip_plan(qsd):
     dims = [50, 60, 70]
     coords, vals = tensor(dims, 40_000, seed=70, zipf=1.1)
