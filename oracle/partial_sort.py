@@ -19,7 +19,7 @@ from __future__ import annotations
 
 from typing import List, Sequence, Tuple
 
-from .plan import quesadilla_calls
+from .plan import quesadilla_calls, topk_steps
 
 Coord = Tuple[int, ...]
 
@@ -113,6 +113,40 @@ def quesadilla_sort(crd: Sequence[Coord], dims: Sequence[int],
             tagged, _ = partial_sort_nonbucketed(tagged, mode, dims[mode])
         else:
             tagged, *_ = partial_sort_bucketed(tagged, prefix, mode, dims[mode])
+    out_crd = [t[:r] for t in tagged]
+    order = [t[r] for t in tagged]
+    out_vals = None if vals is None else [vals[j] for j in order]
+    return out_crd, out_vals, order
+
+
+def topk_sadilla_sort(crd: Sequence[Coord], dims: Sequence[int], sigma: Sequence[int],
+                      K: int, tau: Sequence[int] | None = None, vals: Sequence | None = None):
+    """Top-K-sadilla (Section 3.6) on (crd, vals): Algorithm 3's calls, run
+    with Algorithms 1 and 2, sort the tensor to the order of sigma_1..sigma_K
+    (oracle.plan.topk_target); then every bucket of equal (sigma_1..sigma_K)
+    is sorted completely by (sigma_{K+1}, ..., sigma_r) with a comparison
+    sort. The section's quicksort is not stable; Python's sort, which is,
+    stands in for it, so that duplicate coordinates keep their values in
+    input order as every other path here does."""
+    r = len(sigma)
+    tagged = [tuple(c) + (j,) for j, c in enumerate(crd)]
+    calls, final = topk_steps(sigma, tau, K)
+    for prefix, mode in calls:
+        if len(prefix) == 0:
+            tagged, _ = partial_sort_nonbucketed(tagged, mode, dims[mode])
+        else:
+            tagged, *_ = partial_sort_bucketed(tagged, prefix, mode, dims[mode])
+    if final is not None:
+        prefix, keys = final
+        out: List[Coord] = []
+        j, N = 0, len(tagged)
+        while j < N:  # one bucket of equal prefix at a time
+            e = j + 1
+            while e < N and all(tagged[e][m] == tagged[j][m] for m in prefix):
+                e += 1
+            out.extend(sorted(tagged[j:e], key=lambda t: tuple(t[m] for m in keys)))
+            j = e
+        tagged = out
     out_crd = [t[:r] for t in tagged]
     order = [t[r] for t in tagged]
     out_vals = None if vals is None else [vals[j] for j in order]

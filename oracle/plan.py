@@ -23,6 +23,10 @@ labels; the readings are listed in the design doc):
   ``tau`` its scan test compares against ``f(tau, .)`` instead of
   ``f((1..r), .)``, which is the paper's "without loss of generality"
   relabelling (Section 2.2) written without relabelling.
+* ``topk_target(sigma, tau, K)`` and ``topk_steps(sigma, tau, K)``:
+  Top-K-sadilla (Section 3.6): Algorithm 3's calls that sort the tensor to
+  the order of its first K target modes, then one complete sort of every
+  bucket of equal (sigma_1..sigma_K) by the remaining target modes.
 * ``bfs_min_calls(tau, sigma)``: exhaustive search over every sequence of
   PartialSort calls (all l < k at every intermediate ordering) for the
   lexicographically smallest (#calls, #bucketed calls) that reaches sigma --
@@ -102,6 +106,36 @@ def quesadilla_calls(sigma: Sequence[int],
             k -= 1
         l = l_next
     return calls
+
+
+def topk_target(sigma: Sequence[int], tau: Sequence[int] | None, K: int) -> Tuple[int, ...]:
+    """The complete ordering Top-K-sadilla's first stage sorts to.
+
+    Section 3.6 fixes only its leading modes, sigma_1..sigma_K. The other
+    modes follow here in their tau order: that is where a stable sort by the
+    K leading modes leaves them, and none of them then needs a PartialSort
+    call (each is followed only by modes that also follow it in tau).
+    """
+    sigma = tuple(sigma)
+    tau = tuple(range(len(sigma))) if tau is None else tuple(tau)
+    head = sigma[:max(0, K)]
+    return head + tuple(m for m in tau if m not in head)
+
+
+def topk_steps(sigma: Sequence[int], tau: Sequence[int] | None, K: int):
+    """Top-K-sadilla (Section 3.6) as (calls, final).
+
+    calls: the PartialSort calls Algorithm 3 makes from tau to
+    topk_target(sigma, tau, K). final: (prefix modes, key modes) of the
+    complete sort of every bucket of equal (sigma_1..sigma_K) by
+    (sigma_{K+1}, ..., sigma_r), or None when the first stage already ends
+    in sigma (always for K >= r - 1).
+    """
+    sigma = tuple(sigma)
+    target = topk_target(sigma, tau, K)
+    calls = quesadilla_calls(target, tau)
+    final = None if target == sigma else (sigma[:K], sigma[K:])
+    return calls, final
 
 
 def apply_calls(tau: Sequence[int], calls: Iterable[Call]) -> Tuple[int, ...]:

@@ -174,3 +174,62 @@ def test_literal_quesadilla_equals_stable_sort(r):
             want = oracle.permutation(coords, sigma)
             assert ordr == [int(x) for x in want], (tau, sigma)
             assert out_vals == [int(x) for x in want]
+
+
+def _sorted_under(coords, sigma):
+    return [int(x) for x in np.lexsort([coords[m] for m in reversed(tuple(sigma))])]
+
+
+@pytest.mark.parametrize("r", [3, 4])
+def test_topk_sadilla_equals_stable_sort(r):
+    # Section 3.6: for every K the two stages end in sigma order; ties
+    # (duplicate coordinates) keep their input order
+    rng = np.random.default_rng(70 + r)
+    dims = [int(x) for x in rng.integers(2, 6, size=r)]
+    for tau in [tuple(range(r)), tuple(int(x) for x in rng.permutation(r))]:
+        coords = np.stack([rng.integers(0, d, size=300) for d in dims]).astype(np.int32)
+        coords = coords[:, _sorted_under(coords, tau)]
+        crd = [tuple(int(x) for x in coords[:, j]) for j in range(coords.shape[1])]
+        vals = list(range(len(crd)))
+        for sigma in itertools.permutations(range(r)):
+            want = [int(x) for x in oracle.permutation(coords, sigma)]
+            for K in range(r + 1):
+                _, out_vals, ordr = PS.topk_sadilla_sort(crd, dims, sigma, K, tau, vals)
+                assert ordr == want, (tau, sigma, K)
+                assert out_vals == want
+
+
+@pytest.mark.parametrize("r", [3, 4, 5])
+def test_topk_first_stage_is_the_stable_sort_by_k_modes(r):
+    # the calls of the first stage, run as real stable sorts, leave the data
+    # exactly as one stable sort by (sigma_1..sigma_K) does, and they are never
+    # more than Quesadilla's own
+    rng = np.random.default_rng(80 + r)
+    dims = [3] * r
+    coords = np.stack([rng.integers(0, 3, size=200) for _ in range(r)]).astype(np.int32)
+    tau = tuple(int(x) for x in rng.permutation(r))
+    coords = coords[:, _sorted_under(coords, tau)]
+    crd = [tuple(int(x) for x in coords[:, j]) for j in range(coords.shape[1])]
+    for sigma in itertools.permutations(range(r)):
+        for K in range(r + 1):
+            calls, final = P.topk_steps(sigma, tau, K)
+            target = P.topk_target(sigma, tau, K)
+            assert target[:K] == tuple(sigma[:K])
+            assert P.apply_calls(tau, calls) == target
+            assert len(calls) == P.b(tau, target) <= P.b(tau, sigma)
+            assert not any(P.needs_sort(target, tau, m) for m in target[K:])
+            tagged = [c + (j,) for j, c in enumerate(crd)]
+            for prefix, mode in calls:
+                if prefix:
+                    tagged, *_ = PS.partial_sort_bucketed(tagged, prefix, mode, dims[mode])
+                else:
+                    tagged, _ = PS.partial_sort_nonbucketed(tagged, mode, dims[mode])
+            head = np.stack([coords[m] for m in sigma[:K]]) if K else np.zeros((0, coords.shape[1]))
+            want = [int(x) for x in np.lexsort(head[::-1])] if K else list(range(coords.shape[1]))
+            assert [t[r] for t in tagged] == want, (tau, sigma, K)
+            if K >= r - 1:
+                assert (calls, final) == (P.quesadilla_calls(sigma, tau), None)
+            if K == 0:
+                assert calls == [] and final == (None if tuple(sigma) == tau else ((), tuple(sigma)))
+            if final is not None:
+                assert final == (tuple(sigma[:K]), tuple(sigma[K:]))
