@@ -103,6 +103,13 @@ typedef struct {
                             each bucket of equal prefix by the key (the same
                             result: the group's input is sorted by its
                             prefix); more digit passes, no bucket work */
+  int top_k;             /* K > 0: Top-K-sadilla (Section 3.6): Algorithm 3
+                            sorts to the order of the first K target modes
+                            (the other modes keep their input order), then
+                            every bucket of equal first-K coordinates is
+                            sorted completely by the remaining target modes;
+                            the same result. 0, or K >= order - 1: plain
+                            Quesadilla. 0 <= K <= QSD_MAX_ORDER */
 } qsd_plan_options;
 
 /* Description of a plan (qsd_plan_get_info). */
@@ -144,7 +151,9 @@ typedef struct {
 qsd_status qsd_plan(int order, const int64_t* dims, const int* input_mode_order,
                     const int* target_perm, qsd_plan_t* out);
 
-/* qsd_plan with options (opts may be NULL = defaults). */
+/* qsd_plan with options (opts may be NULL = defaults). Also returns
+ * QSD_ERR_UNSUPPORTED when a group's packed key would need more than 32
+ * digit passes at the chosen digit width (possible only below 8 bits). */
 qsd_status qsd_plan_ex(int order, const int64_t* dims,
                        const int* input_mode_order, const int* target_perm,
                        const qsd_plan_options* opts, qsd_plan_t* out);

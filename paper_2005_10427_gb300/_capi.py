@@ -29,7 +29,7 @@ class PlanOptions(ctypes.Structure):
     _fields_ = [("validate", ctypes.c_int), ("digit_bits", ctypes.c_int),
                 ("local_capacity", ctypes.c_int), ("no_skip", ctypes.c_int),
                 ("tile", ctypes.c_int), ("chunk_tiles", ctypes.c_int),
-                ("global_groups", ctypes.c_int)]
+                ("global_groups", ctypes.c_int), ("top_k", ctypes.c_int)]
 
 
 _A = ctypes.c_int * MAX_ORDER

@@ -34,8 +34,9 @@ bool is_perm(int order, const int* p) {
 }
 
 // Splits the packed key of group g into LSD-first digit passes of at most
-// `digit_bits` bits, as even as possible.
-void schedule_digits(const int64_t* dims, qsd::Group& g, int digit_bits) {
+// `digit_bits` bits, as even as possible. False when that takes more passes
+// than a group holds.
+bool schedule_digits(const int64_t* dims, qsd::Group& g, int digit_bits) {
   int base[QSD_MAX_ORDER], width[QSD_MAX_ORDER];
   int acc = 0;
   for (int i = g.nkeys - 1; i >= 0; --i) {  // last key mode = lowest bits
@@ -46,9 +47,10 @@ void schedule_digits(const int64_t* dims, qsd::Group& g, int digit_bits) {
   g.key_bits = acc;
   if (acc == 0) {
     g.npasses = 0;
-    return;
+    return true;
   }
   int np = (acc + digit_bits - 1) / digit_bits;
+  if (np > qsd::kMaxPasses) return false;
   g.npasses = np;
   int lo = 0;
   for (int p = 0; p < np; ++p) {
@@ -69,6 +71,7 @@ void schedule_digits(const int64_t* dims, qsd::Group& g, int digit_bits) {
     }
     lo = hi;
   }
+  return true;
 }
 
 }  // namespace
@@ -99,6 +102,7 @@ qsd_status qsd_plan_ex(int order, const int64_t* dims,
   if (o.tile != 0 && o.tile != 1024 && o.tile != 2048 && o.tile != 3584 && o.tile != 4096)
     return QSD_ERR_INVALID_ARGUMENT;
   if (o.chunk_tiles < 0 || o.chunk_tiles > 256) return QSD_ERR_INVALID_ARGUMENT;
+  if (o.top_k < 0 || o.top_k > QSD_MAX_ORDER) return QSD_ERR_INVALID_ARGUMENT;
 
   qsd_plan_s* p = new (std::nothrow) qsd_plan_s;
   if (!p) return QSD_ERR_OUT_OF_MEMORY;
@@ -113,17 +117,38 @@ qsd_status qsd_plan_ex(int order, const int64_t* dims,
   p->digit_bits = o.digit_bits ? o.digit_bits : qsd::kRadixBits;
   p->local_capacity = o.local_capacity ? o.local_capacity : 4096;
 
+  // Top-K-sadilla (Section 3.6): Algorithm 3 sorts only to the order of the
+  // first K target modes -- the ordering sigma_1..sigma_K followed by the
+  // other modes in their tau order, where a stable sort by the K modes leaves
+  // them (none of them then needs a call) -- and one last group sorts every
+  // bucket of equal (sigma_1..sigma_K) completely by the remaining target
+  // modes. K >= order - 1 is Quesadilla itself.
+  const int K = (o.top_k > 0 && o.top_k < order - 1) ? o.top_k : order;
+  int tgt[QSD_MAX_ORDER];  // the ordering Algorithm 3 sorts to
+  {
+    unsigned head = 0;
+    for (int i = 0; i < order; ++i) {
+      tgt[i] = target_perm[i];
+      if (i < K) head |= 1u << target_perm[i];
+    }
+    int n = K < order ? K : order;
+    for (int i = 0; i < order && K < order; ++i)
+      if (!(head >> input_mode_order[i] & 1u)) tgt[n++] = input_mode_order[i];
+  }
+  bool topk_group = false;
+  for (int i = 0; i < order; ++i) topk_group |= tgt[i] != target_perm[i];
+
   // f(tau, m) and f(sigma, m) as bit sets: the modes after m (Section 3.4).
   unsigned f_tau[QSD_MAX_ORDER] = {0}, f_sigma[QSD_MAX_ORDER] = {0};
   for (int i = 0; i < order; ++i)
     for (int j = i + 1; j < order; ++j) {
       f_tau[input_mode_order[i]] |= 1u << input_mode_order[j];
-      f_sigma[target_perm[i]] |= 1u << target_perm[j];
+      f_sigma[tgt[i]] |= 1u << tgt[j];
     }
   auto needs_sort = [&](int m) {  // f(sigma, m) not a subset of f(tau, m)
     return (f_sigma[m] & ~f_tau[m]) != 0;
   };
-  auto s = [&](int i) { return target_perm[i - 1]; };  // sigma_i, 1-based
+  auto s = [&](int i) { return tgt[i - 1]; };  // sigma_i, 1-based
 
   if (o.no_skip) {
     // Full LSD radix sort over every mode: r non-bucketed calls, sigma_r
@@ -157,6 +182,13 @@ qsd_status qsd_plan_ex(int order, const int64_t* dims,
       }
       l = l_next;
     }
+    if (topk_group) {  // Top-K-sadilla's complete sort of every bucket
+      qsd::Group& g = p->groups[p->ngroups++];
+      g.prefix_len = K;
+      for (int i = 0; i < K; ++i) g.prefix_modes[i] = target_perm[i];
+      g.nkeys = order - K;
+      for (int i = K; i < order; ++i) g.key_modes[i - K] = target_perm[i];
+    }
     if (o.global_groups) {
       // An equivalent execution: the input of a group is already sorted by
       // its prefix, so one stable sort of the whole tensor by (prefix, key)
@@ -176,7 +208,10 @@ qsd_status qsd_plan_ex(int order, const int64_t* dims,
     }
   }
   for (int i = 0; i < p->ngroups; ++i)
-    schedule_digits(p->dims, p->groups[i], p->digit_bits);
+    if (!schedule_digits(p->dims, p->groups[i], p->digit_bits)) {
+      delete p;
+      return QSD_ERR_UNSUPPORTED;  // a key too wide for the digit width
+    }
   *out = p;
   return QSD_OK;
 }

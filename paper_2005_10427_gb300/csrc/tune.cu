@@ -2,10 +2,12 @@
 //
 // The paper orders plans by the number of partial sorts (Theorems 2-3) and
 // proposes, as future work, choosing by actual cost. Every candidate here
-// computes the same result -- Algorithm 3's calls are fixed -- and differs in
-// how they execute: whether groups with a prefix sort bucket by bucket or as
-// one global sort by (prefix, key), the radix digit width (how many passes),
-// the tile and chunk sizes, and the bucket capacity of the shared-memory sort.
+// computes the same result and differs in how: Quesadilla or Top-K-sadilla
+// for a K (Section 3.6: fewer calls of Algorithm 3, then one complete sort of
+// the buckets of the first K target modes), whether groups with a prefix
+// sort bucket by bucket or as one global sort by (prefix, key), the radix
+// digit width (how many passes), the tile and chunk sizes, and the bucket
+// capacity of the shared-memory sort.
 // Each candidate is timed with CUDA events over real out-of-place
 // transpositions of the caller's data; a coordinate search keeps the fastest.
 #include <cuda_runtime.h>
@@ -28,7 +30,9 @@ bool has_prefix_group(const qsd_plan_s* p) {
   return false;
 }
 
-// The values each option takes in the search (0 = the library's choice).
+// The values each option takes in the search (0 = the library's choice);
+// top_k takes 0 .. order - 2.
+constexpr int kDims = 6;
 const int kStructure[] = {0, 1};
 const int kDigits[] = {8, 7, 6, 5};
 const int kTiles[] = {0, 4096, 3584, 2048};
@@ -36,24 +40,35 @@ const int kCaps[] = {4096, 2048, 8192};
 const int kChunks[] = {4, 8, 2};
 
 template <typename F>
-void for_each_candidate_value(int dim, F f) {
+void for_each_candidate_value(int dim, int order, F f) {
   switch (dim) {
-    case 0: for (int v : kStructure) f(v); break;
-    case 1: for (int v : kDigits) f(v); break;
-    case 2: for (int v : kTiles) f(v); break;
-    case 3: for (int v : kCaps) f(v); break;
-    case 4: for (int v : kChunks) f(v); break;
+    case 0: for (int v = 0; v <= std::max(0, order - 2); ++v) f(v); break;
+    case 1: for (int v : kStructure) f(v); break;
+    case 2: for (int v : kDigits) f(v); break;
+    case 3: for (int v : kTiles) f(v); break;
+    case 4: for (int v : kCaps) f(v); break;
+    case 5: for (int v : kChunks) f(v); break;
   }
 }
 
 int& field(qsd_plan_options& o, int dim) {
   switch (dim) {
-    case 0: return o.global_groups;
-    case 1: return o.digit_bits;
-    case 2: return o.tile;
-    case 3: return o.local_capacity;
+    case 0: return o.top_k;
+    case 1: return o.global_groups;
+    case 2: return o.digit_bits;
+    case 3: return o.tile;
+    case 4: return o.local_capacity;
     default: return o.chunk_tiles;
   }
+}
+
+// Whether the plan under options o has a group sorted bucket by bucket.
+bool has_prefix_group(const qsd_plan_s* base, const qsd_plan_options& o) {
+  qsd_plan_t p = nullptr;
+  if (plan_with(base, o, &p) != QSD_OK) return false;
+  const bool r = has_prefix_group(p);
+  qsd_plan_destroy(p);
+  return r;
 }
 
 }  // namespace
@@ -63,36 +78,37 @@ extern "C" {
 qsd_status qsd_plan_tune_workspace_bytes(qsd_plan_t plan, int64_t nnz, size_t* bytes) {
   if (!plan || !bytes || nnz < 0) return QSD_ERR_INVALID_ARGUMENT;
   size_t best = 0;
-  qsd_plan_options o = plan->opts;
-  // every value of every option (the search never combines more than the
-  // current best with one changed option, but the sizes are small enough to
-  // take the maximum over all single changes from any start)
-  for (int dim = 0; dim < 5; ++dim) {
-    for_each_candidate_value(dim, [&](int v) {
-      qsd_plan_options c = o;
-      field(c, dim) = v;
-      for (int gg = 0; gg < 2; ++gg) {
-        c.global_groups = dim == 0 ? v : gg;
-        qsd_plan_t p = nullptr;
-        if (plan_with(plan, c, &p) != QSD_OK) continue;
-        size_t b = 0;
-        if (qsd_workspace_bytes(p, nnz, &b) == QSD_OK) best = std::max(best, b);
-        qsd_plan_destroy(p);
-      }
-    });
-  }
-  // the largest capacity with the smallest digit: the most chunk groups
-  qsd_plan_options c = o;
-  c.local_capacity = 1024;
-  c.digit_bits = 5;
-  c.chunk_tiles = 2;
-  c.tile = 2048;
-  qsd_plan_t p = nullptr;
-  if (plan_with(plan, c, &p) == QSD_OK) {
+  auto take = [&](const qsd_plan_options& c) {
+    qsd_plan_t p = nullptr;
+    if (plan_with(plan, c, &p) != QSD_OK) return;
     size_t b = 0;
     if (qsd_workspace_bytes(p, nnz, &b) == QSD_OK) best = std::max(best, b);
     qsd_plan_destroy(p);
-  }
+  };
+  // For every structure (top_k, global_groups): every single change of the
+  // other options (the search only ever combines the current best with one
+  // changed option, and the sizes are small enough to take the maximum over
+  // all of them from any start), and the smallest capacity, digit, chunk
+  // and tile together (the most chunk groups).
+  for (int k = 0; k <= std::max(0, plan->order - 2); ++k)
+    for (int gg = 0; gg < 2; ++gg) {
+      qsd_plan_options o = plan->opts;
+      o.top_k = k;
+      o.global_groups = gg;
+      take(o);
+      for (int dim = 2; dim < kDims; ++dim)
+        for_each_candidate_value(dim, plan->order, [&](int v) {
+          qsd_plan_options c = o;
+          field(c, dim) = v;
+          take(c);
+        });
+      qsd_plan_options c = o;
+      c.local_capacity = 1024;
+      c.digit_bits = 5;
+      c.chunk_tiles = 2;
+      c.tile = 2048;
+      take(c);
+    }
   *bytes = best;
   return QSD_OK;
 }
@@ -110,11 +126,13 @@ qsd_status qsd_plan_tune(qsd_plan_t plan, const int32_t* in_coords, int64_t in_s
     cudaEventDestroy(e0);
     return QSD_ERR_CUDA;
   }
-  // ms per transposition under options o (< 0: not runnable in the workspace)
+  // ms per transposition under options o (< 0: no such plan, or not runnable
+  // in the workspace)
   auto measure = [&](const qsd_plan_options& o, float* ms) -> qsd_status {
     *ms = -1.f;
     qsd_plan_t p = nullptr;
     qsd_status s = plan_with(plan, o, &p);
+    if (s == QSD_ERR_UNSUPPORTED) return QSD_OK;  // e.g. too many digits for the key
     if (s != QSD_OK) return s;
     size_t need = 0;
     s = qsd_workspace_bytes(p, nnz, &need);
@@ -141,18 +159,18 @@ qsd_status qsd_plan_tune(qsd_plan_t plan, const int32_t* in_coords, int64_t in_s
   if (!best.chunk_tiles) best.chunk_tiles = 4;
   float best_ms = -1.f;
   qsd_status s = measure(best, &best_ms);
-  const bool prefix = has_prefix_group(plan);
-  for (int dim = 0; dim < 5 && s == QSD_OK; ++dim) {
-    if (dim == 0 && !prefix) continue;  // no bucketed group: one structure only
+  for (int dim = 0; dim < kDims && s == QSD_OK; ++dim) {
+    const bool prefix = has_prefix_group(plan, best);
+    if (dim == 1 && !prefix) continue;  // no bucketed group: one structure only
     // the bucket capacity only matters when a bucket sort runs: a group with
     // a prefix, or a whole tensor small enough for one block
-    if (dim == 3 && (!prefix || best.global_groups) && nnz > 8192) continue;
+    if (dim == 4 && (!prefix || best.global_groups) && nnz > 8192) continue;
     qsd_plan_options base = best;
-    for_each_candidate_value(dim, [&](int v) {
+    for_each_candidate_value(dim, plan->order, [&](int v) {
       if (s != QSD_OK || field(base, dim) == v) return;
       qsd_plan_options c = base;
       field(c, dim) = v;
-      if (dim == 3 && c.global_groups) return;  // no bucket sort to size
+      if (dim == 4 && c.global_groups) return;  // no bucket sort to size
       float ms = -1.f;
       s = measure(c, &ms);
       if (s == QSD_OK && ms >= 0.f && (best_ms < 0.f || ms < best_ms)) {

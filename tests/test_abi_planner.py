@@ -99,6 +99,51 @@ def test_planner_matches_oracle_planner(L, r):
                 [(pre, tuple(k)) for pre, k in groups]
 
 
+def _groups_of(calls):
+    # consecutive calls sharing a prefix, keys most significant first
+    groups = []
+    for pre, mode in calls:
+        if groups and groups[-1][0] == pre:
+            groups[-1][1].insert(0, mode)
+        else:
+            groups.append((pre, [mode]))
+    return [(pre, tuple(k)) for pre, k in groups]
+
+
+@pytest.mark.parametrize("r", [3, 4, 5])
+def test_topk_planner_matches_oracle_steps(L, r):
+    rng = np.random.default_rng(10 + r)
+    taus = [tuple(range(r)), tuple(int(x) for x in rng.permutation(r))]
+    for tau in taus:
+        for sigma in itertools.permutations(range(r)):
+            for K in range(r + 2):
+                inf = qsd.Plan([7] * r, sigma, input_mode_order=tau, top_k=K).info()
+                calls, final = OP.topk_steps(sigma, tau, K if 0 < K < r - 1 else r)
+                assert inf["calls"] == calls, (tau, sigma, K)
+                want = _groups_of(calls) + ([final] if final else [])
+                assert [(g["prefix"], g["keys"]) for g in inf["groups"]] == want, (tau, sigma, K)
+
+
+def test_topk_and_digit_limits(L):
+    with pytest.raises(qsd.QsdError) as e:
+        qsd.Plan([4, 4, 4], (2, 1, 0), top_k=-1)
+    assert e.value.status == 1
+    with pytest.raises(qsd.QsdError) as e:
+        qsd.Plan([4, 4, 4], (2, 1, 0), top_k=9)
+    assert e.value.status == 1
+    # 8 modes of 31 bits in one group: 248 bits, 31 passes of 8 bits, but
+    # more passes than a group holds at 7 bits
+    qsd.Plan([2**31 - 1] * 8, tuple(range(8)), no_skip=True)
+    with pytest.raises(qsd.QsdError) as e:
+        qsd.Plan([2**31 - 1] * 8, tuple(range(8)), no_skip=True, digit_bits=7)
+    assert e.value.status == 2
+    # Top-1 of (2, 0, 3, 1) from the identity: Quesadilla's calls to
+    # (2, 0, 1, 3), then every bucket of mode 2 sorted by (0, 3, 1)
+    inf = qsd.Plan([9] * 4, (2, 0, 3, 1), top_k=1).info()
+    assert inf["calls"] == [((), 2)]
+    assert [(g["prefix"], g["keys"]) for g in inf["groups"]] == [((), (2,)), ((2,), (0, 3, 1))]
+
+
 def test_planner_high_order_sampled(L):
     rng = np.random.default_rng(99)
     for r in (6, 7, 8):

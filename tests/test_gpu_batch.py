@@ -29,7 +29,7 @@ class Item:
     """One tensor of a batch: host arrays, device input, device double buffers."""
 
     def __init__(self, qsd, dims, nnz, seed, sigma, val_kind="f32_normal", zipf=1.1,
-                 tau=None, dup=0.0, pad=0):
+                 tau=None, dup=0.0, pad=0, top_k=0):
         if nnz:
             t = synth.random_coo(dims, nnz, seed, val_kind or "f32_normal", zipf=zipf,
                                  dup_frac=dup, input_order=tau)
@@ -41,7 +41,7 @@ class Item:
                 0, np.float64 if val_kind == "f64_uniform" else np.float32)
         nnz = self.coords.shape[1]  # duplicates add entries
         self.dims, self.sigma, self.nnz = list(dims), tuple(sigma), nnz
-        self.plan = qsd.Plan(dims, sigma, input_mode_order=tau)
+        self.plan = qsd.Plan(dims, sigma, input_mode_order=tau, top_k=top_k)
         r = len(dims)
         width = nnz + pad  # pad > 0: row stride above nnz
         cin = torch.zeros((r, max(width, 1)), dtype=torch.int32, device="cuda")
@@ -163,6 +163,18 @@ def test_batch_non_identity_input_orders(qsd):
              Item(qsd, [50, 60, 70, 8], 30000, 22, (0, 3, 2, 1), tau=(3, 1, 0, 2))]
     b, _ = run_batch(qsd, items)
     check_against_oracle(items, b)
+
+
+def test_batch_of_topk_plans(qsd):
+    # Top-K-sadilla plans (Section 3.6) beside Quesadilla plans in one batch;
+    # digit width 6 re-plans every tensor and keeps top_k
+    items = [Item(qsd, [300, 40, 500, 60], 50000, 31, (2, 0, 3, 1), top_k=1),
+             Item(qsd, [300, 40, 500, 60], 50000, 31, (2, 0, 3, 1)),
+             Item(qsd, [80, 90, 70, 60, 5], 40000, 32, (4, 1, 0, 3, 2), top_k=2),
+             Item(qsd, [2000, 3000, 100], 60000, 33, (0, 2, 1), top_k=1, dup=0.1)]
+    for opts in ({}, dict(digit_bits=6)):
+        b, _ = run_batch(qsd, items, **opts)
+        check_against_oracle(items, b)
 
 
 @pytest.mark.parametrize("opts", [dict(tile=2048), dict(tile=1024, chunk_tiles=3),

@@ -169,6 +169,21 @@ def test_global_groups_give_the_same_result(qsd, r):
         check(qsd, coords, vals, dims, sigma, global_groups=True)
 
 
+@pytest.mark.parametrize("r", [3, 4, 5])
+def test_topk_sadilla_plans(qsd, r):
+    # Section 3.6: Quesadilla to the first K target modes, then a complete
+    # sort of every bucket by the rest; the same result for every K
+    rng = np.random.default_rng(100 + r)
+    dims = [int(x) for x in rng.integers(20, 3000, size=r)]
+    coords, vals = tensor(dims, 120_000, seed=100 + r, zipf=1.0, dup=0.1)
+    sigmas = [tuple(int(x) for x in rng.permutation(r)) for _ in range(5)]
+    for sigma in sigmas:
+        for K in range(1, r - 1):
+            check(qsd, coords, vals, dims, sigma, top_k=K)
+    check(qsd, coords, vals, dims, sigmas[0], top_k=1, global_groups=True)
+    check(qsd, coords, vals, dims, sigmas[1], top_k=1, local_capacity=1024)
+
+
 def test_plan_tuner_result_and_options(qsd):
     dims = [300, 2000, 3000]
     coords, vals = tensor(dims, 300_000, seed=81, zipf=1.1)
@@ -180,6 +195,7 @@ def test_plan_tuner_result_and_options(qsd):
     assert ms > 0
     assert opts["digit_bits"] in (5, 6, 7, 8) and opts["tile"] in (0, 2048, 3584, 4096)
     assert opts["global_groups"] in (0, 1) and opts["chunk_tiles"] in (2, 4, 8)
+    assert opts["top_k"] in (0, 1)
     assert torch.equal(c.cpu(), torch.from_numpy(coords))  # the input is left alone
     gc, gv = qsd.transpose(c.clone(), v.clone(), tuned)
     rc, rv = oracle.transpose(coords, vals, sigma)
