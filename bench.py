@@ -255,6 +255,8 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=0,
                     help="timed runs of the batched workload (default: steps, 5..20)")
     ap.add_argument("--no-csf", action="store_true", help="skip the CSF-levels measurement")
+    ap.add_argument("--no-topk", action="store_true",
+                    help="skip the Quesadilla vs Top-K-sadilla comparison")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the Poisson-stream serving measurement")
     args = ap.parse_args()
@@ -377,6 +379,7 @@ def main():
                "d2h_bytes_per_step": len(plans) * nnz * R}
 
     csf = bench_csf(qsd, t, plans, perms, cb, vbuf, ws, stream) if not args.no_csf else None
+    topk = bench_topk(qsd, wl["dims"], t, perms, cb, vbuf, ws, stream) if not args.no_topk else None
 
     batched = None
     if not args.no_batched:
@@ -425,6 +428,8 @@ def main():
             line["cpu_method"] = cpu_method
         if csf is not None:
             line["csf"] = csf
+        if topk is not None:
+            line["topk"] = topk
         if batched is not None:
             line["batched"] = batched
         if serving is not None:
@@ -639,6 +644,35 @@ def bench_csf(qsd, t, plans, perms, cb, vbuf, ws, stream, reps: int = 5):
             "nodes": n, "gb_s": round((2 * 4 * r * nnz + written) / (ms / 1e3) / 1e9, 1)}
     return {"what": "CSF levels of each transposed output (count, scan, write over the entries)",
             "per_order": per}
+
+
+def bench_topk(qsd, dims, t, perms, cb, vbuf, ws, stream, reps: int = 5):
+    """Quesadilla (K = 0) against Top-K-sadilla (Section 3.6) for every K an
+    order allows (1 .. r - 2) on each target order: device time per single
+    out-of-place call, and the groups each plan runs (prefix, key modes)."""
+    r, nnz = t.coords.shape
+    dev = t.coords.device
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per = {}
+    for sigma in perms:
+        row = {}
+        for K in range(0, max(r - 1, 1)):
+            p = qsd.Plan(dims, sigma, top_k=K)
+            need = p.workspace_bytes(nnz)
+            w = ws if need <= ws.numel() else torch.empty(need, dtype=torch.uint8, device=dev)
+            for _ in range(2):
+                qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, p, w, stream)
+            ev0.record(stream)
+            for _ in range(reps):
+                qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, p, w, stream)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / reps
+            row[f"K{K}"] = {"ms": round(ms, 4), "gnnz_s": round(nnz / (ms / 1e3) / 1e9, 2),
+                            "groups": [["".join(map(str, g["prefix"])), "".join(map(str, g["keys"]))]
+                                       for g in p.info()["groups"]]}
+        per["".join(map(str, sigma))] = row
+    return {"what": "single calls: Quesadilla (K0) and Top-K-sadilla (K >= 1)", "per_order": per}
 
 
 def sampled_check(qsd, t, plans, perms, cb, vbuf, ws, stream):
