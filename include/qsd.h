@@ -238,6 +238,22 @@ qsd_status qsd_transpose_host(const int32_t* host_coords, int64_t host_stride,
                               void* workspace, size_t workspace_bytes,
                               void* stream);
 
+/* qsd_transpose_host without the wait: enqueues the copy in, the
+ * transposition and the copy out on `stream` and returns. The host arrays,
+ * device buffers and workspace must stay untouched until the stream has
+ * passed the call; the device status is read afterwards with
+ * qsd_workspace_status(workspace, stream). With page-locked host arrays,
+ * calls on two streams (each with its own device buffers and workspace)
+ * overlap one call's copy out with the next call's copy in and kernels.
+ * Argument errors are returned at once, as for qsd_transpose_host. */
+qsd_status qsd_transpose_host_async(const int32_t* host_coords, int64_t host_stride,
+                                    const void* host_vals, int32_t* host_out_coords,
+                                    int64_t host_out_stride, void* host_out_vals,
+                                    int64_t nnz, qsd_plan_t plan,
+                                    qsd_coords* dev_coords, qsd_values* dev_vals,
+                                    void* workspace, size_t workspace_bytes,
+                                    void* stream);
+
 /* Waits for `stream`, then reads the status word of a workspace used by
  * qsd_transpose_ws (QSD_OK if no device error was recorded). */
 qsd_status qsd_workspace_status(const void* workspace, void* stream,

@@ -525,6 +525,24 @@ def transpose_host(coords_host, vals_host, plan: Plan, dev_cbuf, dev_vbuf, works
     bandwidth); dev_cbuf / dev_vbuf: two device buffers each; results are
     written into out_coords_host / out_vals_host. Waits for the stream.
     """
+    _transpose_host_call(lib().qsd_transpose_host, "qsd_transpose_host", coords_host, vals_host,
+                         plan, dev_cbuf, dev_vbuf, workspace, out_coords_host, out_vals_host,
+                         stream)
+
+
+def transpose_host_async(coords_host, vals_host, plan: Plan, dev_cbuf, dev_vbuf, workspace,
+                         out_coords_host, out_vals_host, stream=None) -> None:
+    """qsd_transpose_host_async: as transpose_host, but returns once the copies
+    and kernels are enqueued on `stream`. Every tensor passed must stay
+    untouched until the stream has passed the call; workspace_status(workspace,
+    stream) then gives the device status."""
+    _transpose_host_call(lib().qsd_transpose_host_async, "qsd_transpose_host_async", coords_host,
+                         vals_host, plan, dev_cbuf, dev_vbuf, workspace, out_coords_host,
+                         out_vals_host, stream)
+
+
+def _transpose_host_call(fn, name, coords_host, vals_host, plan, dev_cbuf, dev_vbuf, workspace,
+                         out_coords_host, out_vals_host, stream):
     nnz = coords_host.shape[1]
     c = _capi.Coords()
     c.buf[0] = dev_cbuf[0].data_ptr()
@@ -536,7 +554,7 @@ def transpose_host(coords_host, vals_host, plan: Plan, dev_cbuf, dev_vbuf, works
         v.buf[0] = dev_vbuf[0].data_ptr()
         v.buf[1] = dev_vbuf[1].data_ptr()
         v.elem_bytes = _val_bytes(dev_vbuf[0])
-    st = lib().qsd_transpose_host(
+    st = fn(
         ctypes.c_void_p(coords_host.data_ptr()), int(coords_host.stride(0)),
         ctypes.c_void_p(vals_host.data_ptr()) if vals_host is not None else None,
         ctypes.c_void_p(out_coords_host.data_ptr()), int(out_coords_host.stride(0)),
@@ -544,7 +562,7 @@ def transpose_host(coords_host, vals_host, plan: Plan, dev_cbuf, dev_vbuf, works
         int(nnz), plan.handle, ctypes.byref(c), ctypes.byref(v),
         ctypes.c_void_p(workspace.data_ptr()), int(workspace.numel()),
         _stream_handle(stream))
-    _check(st, "qsd_transpose_host")
+    _check(st, name)
 
 
 def workspace_status(workspace, stream=None) -> int:

@@ -108,6 +108,8 @@ SIGNATURES = [
     ("qsd_transpose_noalloc", I, [ctypes.POINTER(Coords), ctypes.POINTER(Values), I64, P, P]),
     ("qsd_transpose_host", I, [P, I64, P, P, I64, P, I64, P, ctypes.POINTER(Coords),
                                ctypes.POINTER(Values), P, ctypes.c_size_t, P]),
+    ("qsd_transpose_host_async", I, [P, I64, P, P, I64, P, I64, P, ctypes.POINTER(Coords),
+                                     ctypes.POINTER(Values), P, ctypes.c_size_t, P]),
     ("qsd_workspace_status", I, [P, P, ctypes.POINTER(I)]),
     ("qsd_get_async_status", I, [P, ctypes.POINTER(I)]),
     ("qsd_plan_tune_workspace_bytes", I, [P, I64, ctypes.POINTER(ctypes.c_size_t)]),

@@ -353,12 +353,12 @@ qsd_status qsd_transpose(qsd_coords* coords, qsd_values* vals, int64_t nnz,
   return s;
 }
 
-qsd_status qsd_transpose_host(const int32_t* host_coords, int64_t host_stride,
-                              const void* host_vals, int32_t* host_out_coords,
-                              int64_t host_out_stride, void* host_out_vals, int64_t nnz,
-                              qsd_plan_t plan, qsd_coords* dev_coords,
-                              qsd_values* dev_vals, void* workspace,
-                              size_t workspace_bytes, void* stream) {
+qsd_status qsd_transpose_host_async(const int32_t* host_coords, int64_t host_stride,
+                                    const void* host_vals, int32_t* host_out_coords,
+                                    int64_t host_out_stride, void* host_out_vals, int64_t nnz,
+                                    qsd_plan_t plan, qsd_coords* dev_coords,
+                                    qsd_values* dev_vals, void* workspace,
+                                    size_t workspace_bytes, void* stream) {
   qsd_status s = check_buffers(dev_coords, dev_vals, nnz, plan);
   if (s != QSD_OK) return s;
   const bool has_vals = dev_vals && dev_vals->elem_bytes != 0;
@@ -389,6 +389,19 @@ qsd_status qsd_transpose_host(const int32_t* host_coords, int64_t host_stride,
                                (size_t)dev_vals->elem_bytes * nnz, cudaMemcpyDeviceToHost,
                                st));
   }
+  return QSD_OK;
+}
+
+qsd_status qsd_transpose_host(const int32_t* host_coords, int64_t host_stride,
+                              const void* host_vals, int32_t* host_out_coords,
+                              int64_t host_out_stride, void* host_out_vals, int64_t nnz,
+                              qsd_plan_t plan, qsd_coords* dev_coords,
+                              qsd_values* dev_vals, void* workspace,
+                              size_t workspace_bytes, void* stream) {
+  qsd_status s = qsd_transpose_host_async(host_coords, host_stride, host_vals, host_out_coords,
+                                          host_out_stride, host_out_vals, nnz, plan, dev_coords,
+                                          dev_vals, workspace, workspace_bytes, stream);
+  if (s != QSD_OK) return s;
   qsd_status dev_status = QSD_OK;
   s = qsd_workspace_status(workspace, stream, &dev_status);
   if (s != QSD_OK) return s;

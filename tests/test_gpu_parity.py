@@ -269,6 +269,32 @@ def test_transpose_host_end_to_end(qsd):
     assert np.array_equal(oc.numpy(), rc) and np.array_equal(ov.numpy(), rv)
 
 
+def test_transpose_host_async_on_two_streams(qsd):
+    # consecutive asynchronous calls alternate between two streams, each with
+    # its own device buffers and workspace; every result equals the oracle's
+    dims = [300, 200, 100]
+    coords, vals = tensor(dims, 90_000, seed=81, zipf=1.1)
+    n = coords.shape[1]
+    hc = torch.from_numpy(coords).pin_memory()
+    hv = torch.from_numpy(vals).pin_memory()
+    sigmas = [(2, 0, 1), (0, 2, 1), (1, 2, 0), (2, 1, 0), (1, 0, 2), (0, 2, 1)]
+    plans = [qsd.Plan(dims, sg) for sg in sigmas]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    cbs = [[torch.empty((3, n), dtype=torch.int32, device="cuda") for _ in range(2)] for _ in range(2)]
+    vbs = [[torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(2)] for _ in range(2)]
+    wss = [torch.empty(max(p.workspace_bytes(n) for p in plans), dtype=torch.uint8, device="cuda")
+           for _ in range(2)]
+    outs = [(torch.empty_like(hc).pin_memory(), torch.empty_like(hv).pin_memory()) for _ in sigmas]
+    for k, (p, (oc, ov)) in enumerate(zip(plans, outs)):
+        i = k % 2  # a stream's calls reuse its buffers in stream order
+        qsd.transpose_host_async(hc, hv, p, cbs[i], vbs[i], wss[i], oc, ov, streams[i])
+    for i in range(2):
+        assert qsd.workspace_status(wss[i], streams[i]) == 0
+    for sg, (oc, ov) in zip(sigmas, outs):
+        rc, rv = oracle.transpose(coords, vals, sg)
+        assert np.array_equal(oc.numpy(), rc) and np.array_equal(ov.numpy(), rv), sg
+
+
 def test_repeated_calls_reuse_workspace(qsd):
     dims = [500, 400, 300]
     coords, vals = tensor(dims, 150_000, seed=90, zipf=1.1)
