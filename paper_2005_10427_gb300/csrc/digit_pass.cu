@@ -111,12 +111,19 @@ k_chunk_hist(const __grid_constant__ PassTensor one, LargeSegs ls,
   const Cols& c = s_it.c;
   const PassDesc& pd = s_it.pd;
   if (!pb.t) copy_words(&s_it, &one, threadIdx.x, kHistThreads);
+  // thread 0 claims one chunk ahead, so the claim's round trip overlaps the
+  // current chunk's work
+  auto claim_next = [&]() {
+    const int idx = atomicAdd(claim, 1);
+    return idx < nc ? (pb.t ? pb.chunks[idx] : idx) : -1;
+  };
+  int next = threadIdx.x == 0 ? claim_next() : -1;
   while (true) {
     for (int i = threadIdx.x; i < kHistWarps * kRadix; i += kHistThreads)
       (&s_hist[0][0])[i] = 0;
     if (threadIdx.x == 0) {
-      const int idx = atomicAdd(claim, 1);
-      s_chunk = idx < nc ? (pb.t ? pb.chunks[idx] : idx) : -1;
+      s_chunk = next;
+      if (next >= 0) next = claim_next();
     }
     __syncthreads();
     const int ch = s_chunk;
@@ -153,7 +160,39 @@ k_chunk_hist(const __grid_constant__ PassTensor one, LargeSegs ls,
       atomicAdd(&s_hist[w][d], 1u);
     }
     const int nvec = (vend - vbeg) >> 2;
-    for (int q0 = threadIdx.x; q0 < nvec; q0 += kHistThreads * 4) {
+    // a digit from one row: 8 vectors (128 bytes) per thread in flight per round
+    if (pd.nfields == 1) {
+      const DigitField fd = pd.f[0];
+      const uint4* col =
+          reinterpret_cast<const uint4*>(c.in + (int64_t)fd.mode * c.in_stride + vbeg);
+      for (int q0 = threadIdx.x; q0 < nvec; q0 += kHistThreads * 8) {
+        uint4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int q = q0 + u * kHistThreads;
+          v[u] = q < nvec ? __ldg(col + q) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (q0 + u * kHistThreads >= nvec) break;
+          const uint32_t e[4] = {field_bits(v[u].x, fd), field_bits(v[u].y, fd),
+                                 field_bits(v[u].z, fd), field_bits(v[u].w, fd)};
+          uint32_t run_d = e[0], run_n = 1;
+#pragma unroll
+          for (int k = 1; k < 4; ++k) {
+            if (e[k] == run_d) {
+              ++run_n;
+            } else {
+              atomicAdd(&s_hist[w][run_d], run_n);
+              run_d = e[k];
+              run_n = 1;
+            }
+          }
+          atomicAdd(&s_hist[w][run_d], run_n);
+        }
+      }
+    }
+    for (int q0 = threadIdx.x; q0 < (pd.nfields == 1 ? 0 : nvec); q0 += kHistThreads * 4) {
       uint4 dv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) dv[u] = make_uint4(0, 0, 0, 0);
