@@ -76,6 +76,37 @@ def test_transpose_argument_errors_without_gpu(L):
     assert L.qsd_workspace_bytes(p.handle, -5, ctypes.byref(out)) == 1
 
 
+def test_host_buffer_calls_check_arguments_before_device_work(L):
+    # both host-buffer calls report argument errors before any copy or kernel
+    # (device pointers here are never dereferenced)
+    p = qsd.Plan([4, 4], [1, 0])
+    c = _capi.Coords()
+    c.stride = 10
+    c.selector = 0
+    host = (ctypes.c_int32 * 20)()
+    for fn in (L.qsd_transpose_host, L.qsd_transpose_host_async):
+        # null device buffers
+        assert fn(host, 10, None, host, 10, None, 10, p.handle, ctypes.byref(c), None,
+                  None, 0, None) == 1
+        c.buf[0], c.buf[1] = 1 << 36, 2 << 36
+        # null host arrays, host strides shorter than nnz
+        assert fn(None, 10, None, host, 10, None, 10, p.handle, ctypes.byref(c), None,
+                  None, 0, None) == 1
+        assert fn(host, 10, None, None, 10, None, 10, p.handle, ctypes.byref(c), None,
+                  None, 0, None) == 1
+        assert fn(host, 9, None, host, 10, None, 10, p.handle, ctypes.byref(c), None,
+                  None, 0, None) == 1
+        assert fn(host, 10, None, host, 9, None, 10, p.handle, ctypes.byref(c), None,
+                  None, 0, None) == 1
+        # values declared but no host value arrays
+        v = _capi.Values()
+        v.buf[0], v.buf[1] = 3 << 36, 4 << 36
+        v.elem_bytes = 4
+        assert fn(host, 10, None, host, 10, None, 10, p.handle, ctypes.byref(c), ctypes.byref(v),
+                  None, 0, None) == 1
+        c.buf[0] = c.buf[1] = None
+
+
 @pytest.mark.parametrize("r", [1, 2, 3, 4, 5])
 def test_planner_matches_oracle_planner(L, r):
     rng = np.random.default_rng(r)
