@@ -97,7 +97,7 @@ typedef struct {
                             once: 1024, 2048, 3584 or 4096 (smaller when the
                             rows do not fit); 0 = automatic */
   int chunk_tiles;       /* tiles per chunk, the unit of the per-chunk digit
-                            counts, 1..256; 0 = automatic (4) */
+                            counts, 1..256; 0 = automatic (2) */
   int global_groups;     /* nonzero: run every group that has a prefix as one
                             global sort by (prefix, key) instead of sorting
                             each bucket of equal prefix by the key (the same
@@ -349,7 +349,7 @@ typedef struct {
   int digit_bits;      /* 0 = each plan's own */
   int local_capacity;  /* 0 = 4096 */
   int tile;            /* 0 = automatic */
-  int chunk_tiles;     /* 0 = 4 */
+  int chunk_tiles;     /* 0 = 2 */
   int no_graph;        /* nonzero: launch directly instead of replaying a graph */
   int use_tuned;       /* nonzero: take the options the tuning cache holds for
                           a batch of this shape, if any (qsd_batch_tune) */

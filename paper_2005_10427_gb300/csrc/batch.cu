@@ -642,7 +642,7 @@ qsd_status qsd_batch_tune(qsd_batch_t b, void* workspace, size_t workspace_bytes
   qsd_batch_options best = c.opts;
   if (!best.local_capacity) best.local_capacity = 4096;
   if (!best.tile) best.tile = c.T;
-  if (!best.chunk_tiles) best.chunk_tiles = 4;
+  if (!best.chunk_tiles) best.chunk_tiles = 2;
   if (!best.digit_bits) best.digit_bits = kRadixBits;
   float best_ms = -1.f;
   qsd_status s = measure(best, &best_ms);
@@ -650,7 +650,7 @@ qsd_status qsd_batch_tune(qsd_batch_t b, void* workspace, size_t workspace_bytes
   const int tiles[] = {4096, 3584, 2048, 1024};
   const int bits[] = {8, 7, 6};
   const int caps[] = {4096, 2048, 8192};
-  const int chunks[] = {4, 8, 2, 16};
+  const int chunks[] = {2, 4, 1, 8};
   for (int dim = 0; dim < 4 && s == QSD_OK; ++dim) {
     const int* vals = dim == 0 ? tiles : dim == 1 ? bits : dim == 2 ? caps : chunks;
     const int nv = dim == 0 || dim == 3 ? 4 : 3;

@@ -37,7 +37,7 @@ const int kStructure[] = {0, 1};
 const int kDigits[] = {8, 7, 6, 5};
 const int kTiles[] = {0, 4096, 3584, 2048};
 const int kCaps[] = {4096, 2048, 8192};
-const int kChunks[] = {4, 8, 2};
+const int kChunks[] = {2, 4, 1};
 
 template <typename F>
 void for_each_candidate_value(int dim, int order, F f) {
@@ -105,7 +105,7 @@ qsd_status qsd_plan_tune_workspace_bytes(qsd_plan_t plan, int64_t nnz, size_t* b
       qsd_plan_options c = o;
       c.local_capacity = 1024;
       c.digit_bits = 5;
-      c.chunk_tiles = 2;
+      c.chunk_tiles = 1;
       c.tile = 2048;
       take(c);
     }
@@ -156,7 +156,7 @@ qsd_status qsd_plan_tune(qsd_plan_t plan, const int32_t* in_coords, int64_t in_s
   qsd_plan_options best = plan->opts;
   if (!best.digit_bits) best.digit_bits = qsd::kRadixBits;
   if (!best.local_capacity) best.local_capacity = 4096;
-  if (!best.chunk_tiles) best.chunk_tiles = 4;
+  if (!best.chunk_tiles) best.chunk_tiles = 2;
   float best_ms = -1.f;
   qsd_status s = measure(best, &best_ms);
   for (int dim = 0; dim < kDims && s == QSD_OK; ++dim) {
