@@ -19,6 +19,8 @@
 // from one tensor into the next, and each takes its tensor's rows and digits.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "kernels.cuh"
 
@@ -50,8 +52,9 @@ struct LsShared {
   uint16_t segid[CAP];
   int first, last, batch_end;
   Cols c;                  // the current batch's tensor: rows
-  const PassDesc* passes;  // and key passes
+  const PassDesc* passes;  // and key passes (pass[])
   int npasses;
+  PassDesc pass[kMaxPasses];
   uint64_t ld;             // the batch's staged rows have landed
   int row_off[kMaxOrder + 1];   // byte offset of element 0 in each staged row
   int row_head[kMaxOrder + 1];  // elements [0, head) and [tail, n) come by plain loads
@@ -88,6 +91,14 @@ __device__ __forceinline__ int warp_search(const int* a, int lo, int hi, int x, 
   return m ? lo + __ffs(m) - 1 : hi;
 }
 
+// Copies np pass descriptors word by word (the lanes of one warp).
+__device__ __forceinline__ void copy_passes(PassDesc* dst, const PassDesc* src, int np, int lane) {
+  static_assert(sizeof(PassDesc) % 4 == 0, "descriptors of whole words");
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int x = lane; x < np * (int)(sizeof(PassDesc) / 4); x += 32) d[x] = s[x];
+}
+
 template <int CAP, int VB>
 __global__ void __launch_bounds__(kLsThreads)
 k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict__ seg_start,
@@ -115,10 +126,12 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
       first = warp_search<false>(seg_start, 0, nseg, win0, lane);
       last = warp_search<false>(seg_start, first, min(nseg, first + (win1 - win0) + 1), win1, lane);
     }
+    // the key passes in shared memory: every digit read takes a field
+    copy_passes(S.pass, pl.pass, pl.npasses, lane);
     if (lane == 0) {
       mbar_init(&S.ld, 1);
       S.c = c1;
-      S.passes = pl.pass;
+      S.passes = S.pass;
       S.npasses = pl.npasses;
       S.first = first;
       S.last = last;
@@ -141,10 +154,11 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
           kt = warp_search<true>(lb.jbase, 0, lb.n + 1, a, lane) - 1;
           kt_end = __ldg(lb.jbase + kt + 1);
           kt_seg = warp_search<false>(seg_start, s + 1, last + 1, kt_end, lane);
+          const int np = lb.t[kt].npasses;
+          copy_passes(S.pass, lb.t[kt].pass, np, lane);
           if (lane == 0) {
             S.c = lb.t[kt].c;
-            S.passes = lb.t[kt].pass;
-            S.npasses = lb.t[kt].npasses;
+            S.npasses = np;
           }
         }
         lim = min(lim, kt_seg);
@@ -220,8 +234,13 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
     int key_bits = 0;
     for (int p = 0; p < S.npasses; ++p) key_bits += S.passes[p].bits;
     bool small = kKeyBits > 0 && !single && key_bits <= kKeyBits;
-    for (int k = s + threadIdx.x; k < e && small; k += kLsThreads)
-      small = seg_start[k + 1] - seg_start[k] <= kTiny;
+    // (the bucket starts go to the second permutation buffer, which the
+    // counting path does not use otherwise)
+    for (int k = s + threadIdx.x; k < e && small; k += kLsThreads) {
+      const int a = seg_start[k];
+      small = seg_start[k + 1] - a <= kTiny;
+      S.perm[1][k - s] = (uint16_t)(a - A);
+    }
     const bool tiny = __syncthreads_and(small);
 
     // Bucket index of every batch position (marks at bucket starts, scanned),
@@ -274,37 +293,49 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
       // Rank by counting: an entry's place in its bucket is the number of the
       // bucket's entries with a smaller packed key, or an equal key earlier in
       // the bucket (stable). Packed keys (the key passes' digits, least
-      // significant first) are built once into the counters' space.
-      uint64_t* key64 = reinterpret_cast<uint64_t*>(S.warp_hist);
-      uint32_t* key32 = S.warp_hist;
-      const bool k64 = kKeyBits == 64 && key_bits > 32;
-      for (int i = threadIdx.x; i < n; i += kLsThreads) {
-        uint64_t key = 0;
-        int off = 0;
-#pragma unroll 1
-        for (int p = 0; p < key_passes; ++p) {
-          const PassDesc& pd = passes[p];
-          uint32_t d = 0;
-          for (int k = 0; k < pd.nfields; ++k) {
-            const DigitField f = pd.f[k];
-            const uint32_t* row =
-                reinterpret_cast<const uint32_t*>(row_smem(f.mode) + S.row_off[f.mode]);
-            d |= field_bits(row[i], f);
+      // significant first) are built once into the counters' space. Each
+      // thread handles its ITEMS entries side by side, so that their
+      // shared-memory reads overlap.
+      using KeyT = typename std::conditional<kKeyBits == 64, uint64_t, uint32_t>::type;
+      KeyT* keys = reinterpret_cast<KeyT*>(S.warp_hist);
+      KeyT key[ITEMS];
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) key[j] = 0;
+      int off = 0;
+      for (int p = 0; p < key_passes; ++p) {
+        const int nf = passes[p].nfields;
+        uint32_t d[ITEMS];
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) d[j] = 0;
+        for (int k = 0; k < nf; ++k) {
+          const DigitField f = passes[p].f[k];
+          const uint32_t* row =
+              reinterpret_cast<const uint32_t*>(row_smem(f.mode) + S.row_off[f.mode]);
+#pragma unroll
+          for (int j = 0; j < ITEMS; ++j) {
+            const int i = threadIdx.x + j * kLsThreads;
+            if (i < n) d[j] |= field_bits(row[i], f);
           }
-          key |= (uint64_t)d << off;
-          off += pd.bits;
         }
-        if (k64) key64[i] = key; else key32[i] = (uint32_t)key;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) key[j] |= (KeyT)d[j] << off;
+        off += passes[p].bits;
+      }
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) {
+        const int i = threadIdx.x + j * kLsThreads;
+        if (i < n) keys[i] = key[j];
       }
       __syncthreads();
+      // every entry walks its bucket (most buckets hold one or two entries)
       for (int i = threadIdx.x; i < n; i += kLsThreads) {
         const int b = nsb > 1 ? S.segid[i] : 0;
-        const int a = seg_start[s + b] - A, z = seg_start[s + b + 1] - A;
-        const uint64_t ki = k64 ? key64[i] : key32[i];
-        int r = a;
+        const int lo = S.perm[1][b], hi = b + 1 < nsb ? S.perm[1][b + 1] : n;
+        const KeyT ki = keys[i];
+        int r = lo;
 #pragma unroll 1
-        for (int y = a; y < z; ++y) {
-          const uint64_t ky = k64 ? key64[y] : key32[y];
+        for (int y = lo; y < hi; ++y) {
+          const KeyT ky = keys[y];
           r += (ky < ki || (ky == ki && y < i)) ? 1 : 0;
         }
         S.perm[0][r] = (uint16_t)i;
