@@ -234,22 +234,23 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
     int key_bits = 0;
     for (int p = 0; p < S.npasses; ++p) key_bits += S.passes[p].bits;
     bool small = kKeyBits > 0 && !single && key_bits <= kKeyBits;
-    // (the bucket starts go to the second permutation buffer, which the
-    // counting path does not use otherwise)
-    for (int k = s + threadIdx.x; k < e && small; k += kLsThreads) {
-      const int a = seg_start[k];
-      small = seg_start[k + 1] - a <= kTiny;
-      S.perm[1][k - s] = (uint16_t)(a - A);
-    }
+    // One read of the batch's bucket starts, while the rows load: marks at
+    // the starts (scanned below into every position's bucket index), the
+    // starts themselves in the second permutation buffer (which the
+    // counting path does not use otherwise) and whether every bucket is tiny.
+    if (nsb > 1)
+      for (int i = threadIdx.x; i < CAP; i += kLsThreads) S.segid[i] = 0;
+    __syncthreads();
+    if (!single)
+      for (int k = s + threadIdx.x; k < e; k += kLsThreads) {
+        const int a = seg_start[k] - A;
+        small = small && seg_start[k + 1] - A - a <= kTiny;
+        S.perm[1][k - s] = (uint16_t)a;
+        if (k > s) S.segid[a] = 1;
+      }
     const bool tiny = __syncthreads_and(small);
 
-    // Bucket index of every batch position (marks at bucket starts, scanned),
-    // while the rows load.
     if (nsb > 1) {
-      for (int i = threadIdx.x; i < CAP; i += kLsThreads) S.segid[i] = 0;
-      __syncthreads();
-      for (int k = s + 1 + threadIdx.x; k < e; k += kLsThreads) S.segid[seg_start[k] - A] = 1;
-      __syncthreads();
       // blocked inclusive scan: thread owns ITEMS consecutive positions
       uint32_t loc[ITEMS], sum = 0;
 #pragma unroll
