@@ -227,3 +227,23 @@ def test_workspace_bytes(L):
     small, big = p.workspace_bytes(1000), p.workspace_bytes(76_000_000)
     assert 0 < small < big < 76_000_000 * 16
     assert p.workspace_bytes(0) > 0
+
+
+def test_tuner_workspace_bound_covers_every_candidate(L):
+    # qsd_plan_tune skips candidates that do not fit the workspace it is
+    # given; the bound it publishes must cover each single change of options
+    # it can try, for every structure (Top-K and global groups included)
+    import itertools as it
+    for dims, sigma in [([12000, 9000, 28000], (0, 2, 1)), ([300, 40, 500, 60], (2, 0, 3, 1)),
+                        ([80, 90, 70, 60, 5], (4, 1, 0, 3, 2))]:
+        r = len(dims)
+        base = qsd.Plan(dims, sigma)
+        for nnz in (5_000, 3_000_000):
+            need = ctypes.c_size_t()
+            assert L.qsd_plan_tune_workspace_bytes(base.handle, nnz, ctypes.byref(need)) == 0
+            for k, gg in it.product(range(max(r - 1, 1)), (False, True)):
+                for opts in [dict(), dict(digit_bits=5), dict(digit_bits=6), dict(tile=2048),
+                             dict(tile=4096), dict(local_capacity=1024 * 8), dict(chunk_tiles=1),
+                             dict(local_capacity=4096, chunk_tiles=4)]:
+                    p = qsd.Plan(dims, sigma, top_k=k, global_groups=gg, **opts)
+                    assert p.workspace_bytes(nnz) <= need.value, (sigma, k, gg, opts, nnz)
