@@ -51,17 +51,19 @@ def build_cpu_method(force: bool = False) -> str:
     return _METHOD_LIB
 
 
-def cpu_method_transpose(coords: np.ndarray, vals, dims, sigma, tau=None, threads: int = 0):
+def cpu_method_transpose(coords: np.ndarray, vals, dims, sigma, tau=None, threads: int = 0,
+                         top_k: int = 0):
     """The paper's method on the host cores (Algorithm 3's calls as counting
-    sorts, parallel as in Section 3.2): same result as transpose()."""
+    sorts, parallel as in Section 3.2; top_k > 0: Top-K-sadilla, Section
+    3.6): same result as transpose()."""
     global _method
     if _method is None:
         build_cpu_method()
         L = ctypes.CDLL(_METHOD_LIB)
         i64, p = ctypes.c_int64, ctypes.c_void_p
-        L.qsd_cpu_method_transpose.argtypes = [ctypes.c_int, i64, p, i64, p, ctypes.c_int, p, p,
-                                               p, ctypes.c_int, p, i64, p]
-        L.qsd_cpu_method_transpose.restype = ctypes.c_int
+        L.qsd_cpu_method_transpose_topk.argtypes = [ctypes.c_int, i64, p, i64, p, ctypes.c_int, p,
+                                                    p, p, ctypes.c_int, ctypes.c_int, p, i64, p]
+        L.qsd_cpu_method_transpose_topk.restype = ctypes.c_int
         L.qsd_cpu_method_threads.argtypes = [ctypes.c_int]
         L.qsd_cpu_method_threads.restype = ctypes.c_int
         _method = L
@@ -73,11 +75,11 @@ def cpu_method_transpose(coords: np.ndarray, vals, dims, sigma, tau=None, thread
     v_in = None if vals is None else np.ascontiguousarray(vals)
     out_v = None if vals is None else np.empty_like(v_in)
     d = np.ascontiguousarray(dims, dtype=np.int64)
-    rc = _method.qsd_cpu_method_transpose(
+    rc = _method.qsd_cpu_method_transpose_topk(
         r, nnz, _ptr(coords), nnz, None if v_in is None else _ptr(v_in), vb, _ptr(d),
         _ptr(np.ascontiguousarray(tau, dtype=np.int32)),
-        _ptr(np.ascontiguousarray(sigma, dtype=np.int32)), int(threads), _ptr(out_c), nnz,
-        None if out_v is None else _ptr(out_v))
+        _ptr(np.ascontiguousarray(sigma, dtype=np.int32)), int(top_k), int(threads), _ptr(out_c),
+        nnz, None if out_v is None else _ptr(out_v))
     if rc != 0:
         raise ValueError("cpu method rejected its arguments")
     return out_c, out_v

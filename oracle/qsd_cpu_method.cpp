@@ -14,6 +14,14 @@
 //     counting-sorted over the range of coordinates it holds.
 // The sorts permute an index array; the rows and values are gathered once at
 // the end.
+//
+// Top-K-sadilla (Section 3.6), qsd_cpu_method_transpose_topk: the calls of
+// Algorithm 3 that sort to the order of the first K target modes (the other
+// modes in their input order), then every bucket of equal (sigma_1..sigma_K)
+// sorted completely by the remaining target modes with a comparison sort,
+// buckets spread over the threads. The section's quicksort is not stable;
+// std::stable_sort stands in so that duplicate coordinates keep their input
+// order here as on every other path.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -93,11 +101,11 @@ void counting_sort_all(const int32_t* key, int64_t dim, std::vector<uint32_t>& i
   idx.swap(tmp);
 }
 
-// Algorithm 2 in parallel: the same sort inside every bucket of equal prefix.
-void counting_sort_buckets(const int32_t* const* prefix, int plen, const int32_t* key,
-                           std::vector<uint32_t>& idx, std::vector<uint32_t>& tmp, int T) {
+// Bucket starts of idx under the prefix modes (entries whose prefix differs
+// from the entry before), with n appended.
+std::vector<int64_t> bucket_starts(const int32_t* const* prefix, int plen,
+                                   const std::vector<uint32_t>& idx) {
   const int64_t n = (int64_t)idx.size();
-  // bucket starts: entries whose prefix differs from the entry before
   std::vector<int64_t> starts;
   for (int64_t j = 0; j < n; ++j) {
     bool s = j == 0;
@@ -105,6 +113,13 @@ void counting_sort_buckets(const int32_t* const* prefix, int plen, const int32_t
     if (s) starts.push_back(j);
   }
   starts.push_back(n);
+  return starts;
+}
+
+// Algorithm 2 in parallel: the same sort inside every bucket of equal prefix.
+void counting_sort_buckets(const int32_t* const* prefix, int plen, const int32_t* key,
+                           std::vector<uint32_t>& idx, std::vector<uint32_t>& tmp, int T) {
+  const std::vector<int64_t> starts = bucket_starts(prefix, plen, idx);
   const int64_t nb = (int64_t)starts.size() - 1;
 #pragma omp parallel num_threads(T)
   {
@@ -149,18 +164,36 @@ void counting_sort_buckets(const int32_t* const* prefix, int plen, const int32_t
 extern "C" {
 
 // Transposes (rows: mode m at coords + m * stride, sorted under tau) into
-// sigma order with the paper's method on `nthreads` threads (0 = all).
-// Returns 0, or -1 on bad arguments.
-int qsd_cpu_method_transpose(int r, int64_t nnz, const int32_t* coords, int64_t stride,
-                             const void* vals, int vb, const int64_t* dims, const int* tau,
-                             const int* sigma, int nthreads, int32_t* out_coords,
-                             int64_t out_stride, void* out_vals) {
-  if (r < 1 || r > 16 || nnz < 0 || nnz > 0xffffffffLL || (vb != 0 && vb != 4 && vb != 8))
+// sigma order with the paper's method on `nthreads` threads (0 = all):
+// Quesadilla for top_k = 0 or top_k >= r - 1, else Top-K-sadilla with
+// K = top_k. Returns 0, or -1 on bad arguments.
+int qsd_cpu_method_transpose_topk(int r, int64_t nnz, const int32_t* coords, int64_t stride,
+                                  const void* vals, int vb, const int64_t* dims, const int* tau,
+                                  const int* sigma, int top_k, int nthreads, int32_t* out_coords,
+                                  int64_t out_stride, void* out_vals) {
+  if (r < 1 || r > 16 || nnz < 0 || nnz > 0xffffffffLL || (vb != 0 && vb != 4 && vb != 8) ||
+      top_k < 0)
     return -1;
   const int T = nthreads_of(nthreads);
+  // the ordering Algorithm 3 sorts to: sigma itself, or for Top-K the first
+  // K target modes followed by the others in their tau order
+  const int K = top_k > 0 && top_k < r - 1 ? top_k : r;
+  int target[16];
+  {
+    unsigned head = 0;
+    int m = 0;
+    for (int i = 0; i < K && i < r; ++i) {
+      target[m++] = sigma[i];
+      head |= 1u << sigma[i];
+    }
+    for (int i = 0; i < r && K < r; ++i)
+      if (!(head >> tau[i] & 1u)) target[m++] = tau[i];
+  }
+  bool complete_sort = false;
+  for (int i = 0; i < r; ++i) complete_sort |= target[i] != sigma[i];
   std::vector<uint32_t> idx((size_t)nnz), tmp((size_t)nnz);
   for (int64_t j = 0; j < nnz; ++j) idx[j] = (uint32_t)j;
-  for (const Call& c : quesadilla_calls(r, tau, sigma)) {
+  for (const Call& c : quesadilla_calls(r, tau, target)) {
     const int32_t* key = coords + (int64_t)c.mode * stride;
     if (c.prefix_len == 0) {
       counting_sort_all(key, dims[c.mode], idx, tmp, T);
@@ -170,6 +203,22 @@ int qsd_cpu_method_transpose(int r, int64_t nnz, const int32_t* coords, int64_t 
       counting_sort_buckets(prefix, c.prefix_len, key, idx, tmp, T);
     }
   }
+  if (complete_sort) {  // Top-K-sadilla's second stage
+    const int32_t* prefix[16];
+    for (int q = 0; q < K; ++q) prefix[q] = coords + (int64_t)sigma[q] * stride;
+    const std::vector<int64_t> starts = bucket_starts(prefix, K, idx);
+    const int64_t nb = (int64_t)starts.size() - 1;
+    auto less = [&](uint32_t x, uint32_t y) {
+      for (int q = K; q < r; ++q) {
+        const int32_t* row = coords + (int64_t)sigma[q] * stride;
+        if (row[x] != row[y]) return row[x] < row[y];
+      }
+      return false;
+    };
+#pragma omp parallel for num_threads(T) schedule(guided)
+    for (int64_t b = 0; b < nb; ++b)
+      std::stable_sort(idx.begin() + starts[b], idx.begin() + starts[b + 1], less);
+  }
 #pragma omp parallel for num_threads(T)
   for (int64_t j = 0; j < nnz; ++j) {
     for (int m = 0; m < r; ++m) out_coords[(int64_t)m * out_stride + j] = coords[(int64_t)m * stride + idx[j]];
@@ -178,6 +227,14 @@ int qsd_cpu_method_transpose(int r, int64_t nnz, const int32_t* coords, int64_t 
                   static_cast<const uint8_t*>(vals) + (size_t)idx[j] * vb, vb);
   }
   return 0;
+}
+
+int qsd_cpu_method_transpose(int r, int64_t nnz, const int32_t* coords, int64_t stride,
+                             const void* vals, int vb, const int64_t* dims, const int* tau,
+                             const int* sigma, int nthreads, int32_t* out_coords,
+                             int64_t out_stride, void* out_vals) {
+  return qsd_cpu_method_transpose_topk(r, nnz, coords, stride, vals, vb, dims, tau, sigma, 0,
+                                       nthreads, out_coords, out_stride, out_vals);
 }
 
 int qsd_cpu_method_threads(int nthreads) { return nthreads_of(nthreads); }

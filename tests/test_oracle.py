@@ -191,3 +191,22 @@ def test_cpu_method_non_identity_input_order():
         a = oracle.transpose(c, v, sigma)
         b = oracle.cpu_method_transpose(c, v, dims, sigma, tau=tau)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), sigma
+
+
+@pytest.mark.parametrize("r", [3, 4, 5])
+def test_cpu_method_topk_sadilla_equals_oracle(r):
+    # Top-K-sadilla on the host (Section 3.6): Algorithm 3's calls to the
+    # first K target modes, then a comparison sort of every bucket; the same
+    # result for every K, with duplicates, on one and on several threads
+    dims = [13, 7, 29, 5, 3][:r]
+    t = synth.random_coo(dims, 2500, seed=120 + r, dup_frac=0.2, zipf=1.1)
+    c, v = t.coords.numpy(), t.vals.numpy()
+    rng = np.random.default_rng(r)
+    for sigma in [tuple(int(x) for x in rng.permutation(r)) for _ in range(6)]:
+        a = oracle.transpose(c, v, sigma)
+        for K in range(r + 1):
+            for threads in (1, 3):
+                b = oracle.cpu_method_transpose(c, v, dims, sigma, threads=threads, top_k=K)
+                assert np.array_equal(a[0], b[0]), (sigma, K, threads)
+                assert np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
+
