@@ -215,9 +215,17 @@ int qsd_cpu_method_transpose_topk(int r, int64_t nnz, const int32_t* coords, int
       }
       return false;
     };
+    // buckets over the threads: dynamic scheduling for K = 1, guided for
+    // K > 1 (more and smaller buckets), as the paper's evaluation does
+    if (K == 1) {
+#pragma omp parallel for num_threads(T) schedule(dynamic, 64)
+      for (int64_t b = 0; b < nb; ++b)
+        std::stable_sort(idx.begin() + starts[b], idx.begin() + starts[b + 1], less);
+    } else {
 #pragma omp parallel for num_threads(T) schedule(guided)
-    for (int64_t b = 0; b < nb; ++b)
-      std::stable_sort(idx.begin() + starts[b], idx.begin() + starts[b + 1], less);
+      for (int64_t b = 0; b < nb; ++b)
+        std::stable_sort(idx.begin() + starts[b], idx.begin() + starts[b + 1], less);
+    }
   }
 #pragma omp parallel for num_threads(T)
   for (int64_t j = 0; j < nnz; ++j) {
