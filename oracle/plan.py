@@ -4,10 +4,10 @@ TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
 bench's CPU-baseline leg; never by the product path. Shares no code with the
 C++ planner in the library.
 
-Everything here follows Section 3.4 ("Minimizing Partial Sorts") and
-Section 3.5 (Algorithm 3, QuesadillaSort) in the paper's notation, with
+Everything here follows Section 3.4 (minimizing the number of partial sorts)
+and Section 3.5 (Algorithm 3, QuesadillaSort) in the paper's notation, with
 orderings written as tuples of 0-based mode labels (the paper writes 1-based
-labels; the readings are listed in the design doc):
+labels):
 
 * ``f(tau, p)``: the set of modes that follow ``p`` in the complete ordering
   ``tau`` (Section 3.4.1, definition of f).

@@ -1,7 +1,7 @@
 """The bench's multi-process path on the CPU (gloo, world size 2): every rank
 gets the slowest rank's time, the whole-job value counts every rank's
-entries, and only rank 0 of the reference arm does any work. (On a GPU machine
-the same code runs one rank per GPU over NCCL.)"""
+entries, and only rank 0 of the reference arm does any work. (With GPUs the
+same code runs one rank per GPU over NCCL.)"""
 import io
 import contextlib
 import os
