@@ -307,10 +307,12 @@ k_chunk_scan(LargeSegs ls, uint32_t* __restrict__ chunk_hist,
 //                      loads its rows' unaligned edges and starts bulk
 //                      copies of the aligned bodies into the slot's staging
 //                      buffer (NS slots);
-//   rankers (8 warps)  compute the digits of tile k+1, rank them stably and
+//   rankers            compute the digits of tile k+1, rank them stably and
 //                      turn the chunk's running output slots into each
 //                      sorted position's destination;
-//   writers (8 warps)  write tile k's rows through the inverse permutation.
+//   writers            write tile k's rows through the inverse permutation.
+// (16 ranking and 15 writing warps for tiles of 2048 entries and more, 8 and
+// 8 for tiles of 1024.)
 // Ranking and writing overlap, and the copies run NS-1 tiles ahead, so
 // neither the ranking latency nor the load latency is on the critical path.
 // Hand-offs use mbarriers (every wait bounded); the rankers synchronise
