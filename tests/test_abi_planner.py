@@ -168,6 +168,10 @@ def test_topk_and_digit_limits(L):
     with pytest.raises(qsd.QsdError) as e:
         qsd.Plan([2**31 - 1] * 8, tuple(range(8)), no_skip=True, digit_bits=7)
     assert e.value.status == 2
+    # no_skip (the full radix sort) takes precedence over top_k
+    inf = qsd.Plan([9] * 4, (2, 0, 3, 1), top_k=1, no_skip=True).info()
+    assert inf["num_calls"] == 4 and [(g["prefix"], g["keys"]) for g in inf["groups"]] == \
+        [((), (2, 0, 3, 1))]
     # Top-1 of (2, 0, 3, 1) from the identity: Quesadilla's calls to
     # (2, 0, 1, 3), then every bucket of mode 2 sorted by (0, 3, 1)
     inf = qsd.Plan([9] * 4, (2, 0, 3, 1), top_k=1).info()
