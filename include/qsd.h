@@ -109,7 +109,8 @@ typedef struct {
                             every bucket of equal first-K coordinates is
                             sorted completely by the remaining target modes;
                             the same result. 0, or K >= order - 1: plain
-                            Quesadilla. 0 <= K <= QSD_MAX_ORDER */
+                            Quesadilla; ignored under no_skip.
+                            0 <= K <= QSD_MAX_ORDER */
 } qsd_plan_options;
 
 /* Description of a plan (qsd_plan_get_info). */
