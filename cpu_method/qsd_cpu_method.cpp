@@ -1,7 +1,7 @@
-// The paper's CPU method, restated in C++ for timing on the host cores (test
-// and bench infrastructure like the rest of oracle/; it shares no code with
-// the CUDA library). It is not the oracle: the oracle is the stable sort of
-// the definition (qsd_oracle.cpp), and the tests check this method against it.
+// The paper's CPU method, restated in C++ for timing on the host cores (bench
+// and test infrastructure; it shares no code with the CUDA library). It is
+// not the oracle: the oracle is the stable sort of the definition, and the
+// tests check this method against it.
 //
 // Algorithm 3 (QuesadillaSort) gives the PartialSort calls; each call runs as
 //   - no prefix (l = 0): Algorithm 1, a stable counting sort of the whole

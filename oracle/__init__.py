@@ -5,10 +5,7 @@ use this package. It shares no code with the CUDA library: the transposition
 oracle is ``qsd_oracle.cpp`` (a stable sort under the target-order
 lexicographic comparator, Section 2), the planner oracle is ``plan.py``
 (Algorithm 3 and an exhaustive search, Sections 3.4-3.5), ``partial_sort``
-holds Algorithms 1 and 2 as literal loops and ``csf`` the CSF levels. Beside
-them, ``qsd_cpu_method.cpp`` restates the paper's own CPU method (Algorithms
-1-3 as parallel counting sorts) for timing on the host cores; it is checked
-against the oracle, not used as one.
+holds Algorithms 1 and 2 as literal loops and ``csf`` the CSF levels.
 """
 from __future__ import annotations
 
@@ -33,61 +30,6 @@ def build(force: bool = False) -> str:
                         _SRC, "-o", tmp], check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
-
-
-_METHOD_SRC = os.path.join(_HERE, "qsd_cpu_method.cpp")
-_METHOD_LIB = os.path.join(_HERE, "libqsd_cpu_method.so")
-_method = None
-
-
-def build_cpu_method(force: bool = False) -> str:
-    """Compiles the paper's CPU method (qsd_cpu_method.cpp, OpenMP) with g++."""
-    if force or not os.path.exists(_METHOD_LIB) or (
-            os.path.getmtime(_METHOD_LIB) < os.path.getmtime(_METHOD_SRC)):
-        tmp = _METHOD_LIB + f".tmp{os.getpid()}"
-        subprocess.run(["g++", "-O2", "-std=c++17", "-fopenmp", "-shared", "-fPIC",
-                        _METHOD_SRC, "-o", tmp], check=True)
-        os.replace(tmp, _METHOD_LIB)
-    return _METHOD_LIB
-
-
-def cpu_method_transpose(coords: np.ndarray, vals, dims, sigma, tau=None, threads: int = 0,
-                         top_k: int = 0):
-    """The paper's method on the host cores (Algorithm 3's calls as counting
-    sorts, parallel as in Section 3.2; top_k > 0: Top-K-sadilla, Section
-    3.6): same result as transpose()."""
-    global _method
-    if _method is None:
-        build_cpu_method()
-        L = ctypes.CDLL(_METHOD_LIB)
-        i64, p = ctypes.c_int64, ctypes.c_void_p
-        L.qsd_cpu_method_transpose_topk.argtypes = [ctypes.c_int, i64, p, i64, p, ctypes.c_int, p,
-                                                    p, p, ctypes.c_int, ctypes.c_int, p, i64, p]
-        L.qsd_cpu_method_transpose_topk.restype = ctypes.c_int
-        L.qsd_cpu_method_threads.argtypes = [ctypes.c_int]
-        L.qsd_cpu_method_threads.restype = ctypes.c_int
-        _method = L
-    coords = np.ascontiguousarray(coords, dtype=np.int32)
-    r, nnz = coords.shape
-    tau = list(range(r)) if tau is None else list(tau)
-    out_c = np.empty_like(coords)
-    vb = 0 if vals is None else vals.dtype.itemsize
-    v_in = None if vals is None else np.ascontiguousarray(vals)
-    out_v = None if vals is None else np.empty_like(v_in)
-    d = np.ascontiguousarray(dims, dtype=np.int64)
-    rc = _method.qsd_cpu_method_transpose_topk(
-        r, nnz, _ptr(coords), nnz, None if v_in is None else _ptr(v_in), vb, _ptr(d),
-        _ptr(np.ascontiguousarray(tau, dtype=np.int32)),
-        _ptr(np.ascontiguousarray(sigma, dtype=np.int32)), int(top_k), int(threads), _ptr(out_c),
-        nnz, None if out_v is None else _ptr(out_v))
-    if rc != 0:
-        raise ValueError("cpu method rejected its arguments")
-    return out_c, out_v
-
-
-def cpu_method_threads(threads: int = 0) -> int:
-    cpu_method_transpose(np.zeros((1, 1), np.int32), None, [1], [0])  # loads the library
-    return int(_method.qsd_cpu_method_threads(int(threads)))
 
 
 def lib():

@@ -13,6 +13,7 @@ import os
 import numpy as np
 import pytest
 
+import cpu_method
 import oracle
 import synth
 
@@ -177,7 +178,7 @@ def test_cpu_method_equals_oracle(r):
     for sigma in itertools.permutations(range(r)):
         a = oracle.transpose(c, v, sigma)
         for threads in (1, 3):
-            b = oracle.cpu_method_transpose(c, v, dims, sigma, threads=threads)
+            b = cpu_method.transpose(c, v, dims, sigma, threads=threads)
             assert np.array_equal(a[0], b[0]), (sigma, threads)
             assert np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
 
@@ -189,7 +190,7 @@ def test_cpu_method_non_identity_input_order():
     c, v = t.coords.numpy(), t.vals.numpy()
     for sigma in itertools.permutations(range(4)):
         a = oracle.transpose(c, v, sigma)
-        b = oracle.cpu_method_transpose(c, v, dims, sigma, tau=tau)
+        b = cpu_method.transpose(c, v, dims, sigma, tau=tau)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), sigma
 
 
@@ -206,7 +207,7 @@ def test_cpu_method_topk_sadilla_equals_oracle(r):
         a = oracle.transpose(c, v, sigma)
         for K in range(r + 1):
             for threads in (1, 3):
-                b = oracle.cpu_method_transpose(c, v, dims, sigma, threads=threads, top_k=K)
+                b = cpu_method.transpose(c, v, dims, sigma, threads=threads, top_k=K)
                 assert np.array_equal(a[0], b[0]), (sigma, K, threads)
                 assert np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
 
