@@ -218,9 +218,14 @@ qsd_status qsd_transpose_from_ws(const int32_t* in_coords, int64_t in_stride,
  * the parts that must start at zero, so calls that may overlap on the GPU
  * (different streams, or streams not ordered with each other) race and must
  * not be issued; calls ordered on one stream are fine. The first call on each
- * device resolves the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture. The launch profiler
- * (qsd_profile_enable) must be off, as it allocates its own buffers.
+ * device resolves the array's device address (cudaGetSymbolAddress) and
+ * keeps it for the life of the process; make that first call before any
+ * stream capture, and do not call this entry point after a reset of the
+ * device's primary context (cudaDeviceReset), which reloads the module and
+ * leaves the kept address stale. While the launch profiler
+ * (qsd_profile_enable) is on, the call returns QSD_ERR_UNSUPPORTED before
+ * anything is enqueued, because the profiler allocates buffers of its own.
+ * The array lies outside any memory budget of the serving loop below.
  * Arguments, result buffers and errors are as for qsd_transpose_ws. */
 qsd_status qsd_transpose_noalloc(qsd_coords* coords, qsd_values* vals,
                                  int64_t nnz, qsd_plan_t plan, void* stream);
@@ -263,6 +268,28 @@ qsd_status qsd_workspace_status(const void* workspace, void* stream,
 /* Waits for `stream`, then returns and clears the current device's sticky
  * status word, which every transpose on that device ORs its errors into. */
 qsd_status qsd_get_async_status(void* stream, qsd_status* out);
+
+/* ---- Bounded waits: test-only controls ----
+ * Every wait of a kernel on another part of itself (a staging buffer that a
+ * bulk copy fills, a hand-off between its warps) gives up after a limit,
+ * records QSD_ERR_TIMEOUT in the device status word and returns; no kernel
+ * traps, and the context stays usable. These two calls exist so that a test
+ * can make such a wait expire on purpose and watch the status. They are
+ * process-wide, apply to the current device, synchronise with it, and must
+ * not be called while library work is in flight. (No counterpart in the
+ * paper.)
+ *
+ * qsd_debug_set_spin_limit_ns: the limit of every bounded wait, in ns;
+ * 0 restores the default (2 s). At most 60 s (else
+ * QSD_ERR_INVALID_ARGUMENT).
+ * qsd_debug_set_stall: 1 = from the next launch on, block 0 of the digit-pass
+ * move kernel arms its first staging slot for the slot's bulk copies but
+ * issues none of them, so every wait on that slot expires and the block's
+ * warps leave through their abort path (the pass's output is then
+ * undefined and the status word reads QSD_ERR_TIMEOUT); 0 = off (default).
+ * Other values: QSD_ERR_INVALID_ARGUMENT. */
+qsd_status qsd_debug_set_spin_limit_ns(uint64_t limit_ns);
+qsd_status qsd_debug_set_stall(int stall);
 
 /* ---- Plan tuner ----
  * The paper ranks plans by their number of partial sorts and leaves choosing
@@ -412,7 +439,9 @@ void qsd_batch_destroy(qsd_batch_t batch);
  * (continuous batching). Each result is bit for bit the one a single
  * qsd_transpose call gives. Results stay in the server's memory until
  * released. Times are seconds of qsd_server_clock(); completion times come
- * from CUDA events on the device. */
+ * from CUDA events on the device. The budget covers the server's own
+ * reservation only: the 64 MiB scratch array of qsd_transpose_noalloc, which
+ * every GPU loading this library holds, is not counted in it. */
 typedef struct qsd_server_s* qsd_server_t;
 
 typedef struct {

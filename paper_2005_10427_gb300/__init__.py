@@ -580,6 +580,17 @@ def get_async_status(stream=None) -> int:
     return int(out.value)
 
 
+def debug_set_spin_limit_ns(limit_ns: int) -> None:
+    """Test-only: the limit of every bounded device wait (0 = default 2 s)."""
+    _check(lib().qsd_debug_set_spin_limit_ns(int(limit_ns)), "qsd_debug_set_spin_limit_ns")
+
+
+def debug_set_stall(stall: int) -> None:
+    """Test-only: 1 = the move kernel's block 0 never fills its first staging
+    slot, so its waits expire (QSD_ERR_TIMEOUT); 0 = off."""
+    _check(lib().qsd_debug_set_stall(int(stall)), "qsd_debug_set_stall")
+
+
 def profile_enable(on: bool = True) -> None:
     """Records CUDA-event timings of every library kernel launch (qsd_profile_*)."""
     _check(lib().qsd_profile_enable(int(bool(on))), "qsd_profile_enable")

@@ -1,6 +1,6 @@
-// Device helpers shared by the kernels: status word, bounded waits,
-// relaxed flag words for decoupled look-back, radix digit extraction and a
-// stable block-wide ranking of radix digits.
+// Device helpers shared by the kernels: status word, bounded waits, bulk
+// copies, radix digit extraction and a stable block-wide ranking of radix
+// digits.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -22,64 +22,23 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
   return t;
 }
 
-// Every spin in this library gives up after this long and records
-// QSD_ERR_TIMEOUT (a legitimate wait lasts microseconds).
+// Every spin in this library gives up after a limit (2 s by default; a
+// legitimate wait lasts microseconds) and records QSD_ERR_TIMEOUT. Without
+// relocatable device code each translation unit holds its own copy of these
+// words; qsd_debug_set_spin_limit_ns and qsd_debug_set_stall set every copy
+// through each unit's set_debug_words().
 constexpr uint64_t kSpinLimitNs = 2000000000ull;  // 2 s
+static __device__ unsigned long long g_spin_limit_ns = kSpinLimitNs;
+// Test-only: 1 = the first tile the move kernel's block 0 stages is armed
+// for its bulk copies but none is issued, so every wait on that staging slot
+// expires (the abort path of the bounded waits runs).
+static __device__ int g_debug_stall = 0;
 
-// ---------------------------------------------------------------------------
-// Look-back words: bits 31..30 = state, bits 29..0 = count.
-constexpr uint32_t kLbNone = 0u;
-constexpr uint32_t kLbAggregate = 1u << 30;
-constexpr uint32_t kLbInclusive = 2u << 30;
-constexpr uint32_t kLbStateMask = 3u << 30;
-constexpr uint32_t kLbCountMask = (1u << 30) - 1;
-
-__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
-  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Waits (bounded) until the word at p has a nonzero state and returns it.
-// On timeout records QSD_ERR_TIMEOUT and returns an inclusive word of 0 so
-// the caller's walk ends.
-__device__ __forceinline__ uint32_t wait_flag(const uint32_t* p, unsigned* status) {
-  uint32_t v = ld_relaxed(p);
-  if (v & kLbStateMask) return v;
-  uint64_t t0 = global_timer_ns();
-  unsigned spins = 0;
-  while (true) {
-    v = ld_relaxed(p);
-    if (v & kLbStateMask) return v;
-    if ((++spins & 63u) == 0) {
-      if (global_timer_ns() - t0 > kSpinLimitNs) {
-        set_status(status, QSD_ERR_TIMEOUT);
-        return kLbInclusive;
-      }
-      __nanosleep(64);
-    }
-  }
-}
-
-// As wait_flag, but reports whether the word was published (false: timed out,
-// status recorded).
-__device__ __forceinline__ bool wait_flag_ok(const uint32_t* p, unsigned* status) {
-  if (ld_relaxed(p) & kLbStateMask) return true;
-  uint64_t t0 = global_timer_ns();
-  unsigned spins = 0;
-  while (!(ld_relaxed(p) & kLbStateMask)) {
-    if ((++spins & 63u) == 0) {
-      if (global_timer_ns() - t0 > kSpinLimitNs) {
-        set_status(status, QSD_ERR_TIMEOUT);
-        return false;
-      }
-      __nanosleep(32);
-    }
-  }
-  return true;
+// Host side: sets this translation unit's copies on the current device.
+static inline cudaError_t set_debug_words(unsigned long long limit_ns, int stall) {
+  cudaError_t e = cudaMemcpyToSymbol(g_spin_limit_ns, &limit_ns, sizeof(limit_ns));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_debug_stall, &stall, sizeof(stall));
+  return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -126,8 +85,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned* status) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
+  const uint64_t limit = *(volatile unsigned long long*)&g_spin_limit_ns;
   while (!mbar_try_wait(bar, parity)) {
-    if (global_timer_ns() - t0 > kSpinLimitNs) {
+    if (global_timer_ns() - t0 > limit) {
       set_status(status, QSD_ERR_TIMEOUT);
       return false;
     }

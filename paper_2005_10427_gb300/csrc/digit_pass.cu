@@ -416,6 +416,9 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
   if (warp == kWsRankWarps + kWsWriteWarps) {
     // ---------------- producer ----------------
     int ch = 0, k = 0, ntile = 0, issued = 0, drain_from = 0;
+    // test-only stall (qsd_debug_set_stall): block 0 arms its first slot
+    // for the copies of its first tile but issues none of them
+    const bool stall = blockIdx.x == 0 && *(volatile int*)&g_debug_stall == 1;
     // the next chunk: an index into the pass's list, -1 when none is left
     auto claim_chunk = [&]() {
       int idx = 0;
@@ -522,9 +525,10 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
         __syncwarp();
         if (lane == 0) mbar_arrive_expect_tx(bar, total);
         else mbar_arrive(bar);
-        if (offs && lane == 31)
+        const bool skip = stall && q == 0;
+        if (offs && lane == 31 && !skip)
           bulk_g2s(ts.off0, chunk_off + (size_t)ch * kRadix, kRadix * sizeof(uint32_t), bar);
-        if (mine && bytes) {
+        if (mine && bytes && !skip) {
           const int e = lane < c.order ? 4 : VB;
           bulk_g2s(buf + (size_t)lane * row_slot<T>(4) + rp.off + (size_t)rp.head * e,
                    reinterpret_cast<const void*>(row_base(c, lane) + (uintptr_t)(start + rp.head) * e),
@@ -759,6 +763,10 @@ cudaError_t launch_chunk_scan(const LargeSegs& ls, uint32_t* chunk_hist,
   if (grid < 1) grid = 1;
   k_chunk_scan<<<grid, kRadix, 0, stream>>>(ls, chunk_hist, group_sum, pb);
   return cudaGetLastError();
+}
+
+cudaError_t debug_words_digit_pass(unsigned long long limit_ns, int stall) {
+  return set_debug_words(limit_ns, stall);
 }
 
 cudaError_t launch_digit_move(const Cols& c, const LargeSegs& ls, const PassDesc& pd,

@@ -446,6 +446,8 @@ qsd_status qsd_transpose_noalloc(qsd_coords* coords, qsd_values* vals, int64_t n
   if (s != QSD_OK) return s;
   const Layout L = layout_for(plan, nnz, vals ? vals->elem_bytes : 0);
   if (L.total > kNoAllocScratchBytes) return QSD_ERR_WORKSPACE_TOO_SMALL;
+  // the launch profiler allocates pinned host memory and events of its own
+  if (prof_enabled()) return QSD_ERR_UNSUPPORTED;
   void* ws = nullptr;
   s = noalloc_scratch(&ws);
   if (s != QSD_OK) return s;
@@ -461,6 +463,38 @@ qsd_status qsd_workspace_status(const void* workspace, void* stream, qsd_status*
   QSD_CUDA(cudaStreamSynchronize(st));
   *out = (qsd_status)v;
   return QSD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Test-only knobs of the bounded waits (no counterpart in the paper).
+namespace {
+std::mutex g_debug_mu;
+unsigned long long g_debug_limit = 0;  // 0 = the default limit
+int g_debug_stall_on = 0;
+
+qsd_status push_debug_words() {
+  const unsigned long long lim = g_debug_limit ? g_debug_limit : 2000000000ull;  // default 2 s
+  if (qsd::debug_words_digit_pass(lim, g_debug_stall_on) != cudaSuccess ||
+      qsd::debug_words_local_sort(lim, g_debug_stall_on) != cudaSuccess) {
+    cudaGetLastError();
+    return QSD_ERR_CUDA;
+  }
+  return QSD_OK;
+}
+}  // namespace
+
+qsd_status qsd_debug_set_spin_limit_ns(uint64_t limit_ns) {
+  if (limit_ns > 60ull * 1000000000ull) return QSD_ERR_INVALID_ARGUMENT;
+  std::lock_guard<std::mutex> lk(g_debug_mu);
+  g_debug_limit = limit_ns;
+  return push_debug_words();
+}
+
+qsd_status qsd_debug_set_stall(int stall) {
+  if (stall != 0 && stall != 1) return QSD_ERR_INVALID_ARGUMENT;
+  std::lock_guard<std::mutex> lk(g_debug_mu);
+  g_debug_stall_on = stall;
+  return push_debug_words();
 }
 
 qsd_status qsd_get_async_status(void* stream, qsd_status* out) {

@@ -209,6 +209,11 @@ int prof_begin(const ProfTag& tag, cudaStream_t st);
 void prof_end(int rec, cudaStream_t st);
 
 cudaError_t launch_fold_status(const unsigned* ws_status, cudaStream_t stream);
+
+// Test-only words of each translation unit with bounded waits: the spin
+// limit (ns) and the move kernel's stall (qsd_debug_set_*).
+cudaError_t debug_words_digit_pass(unsigned long long limit_ns, int stall);
+cudaError_t debug_words_local_sort(unsigned long long limit_ns, int stall);
 cudaError_t read_and_clear_sticky(unsigned* out, cudaStream_t stream);
 
 }  // namespace qsd

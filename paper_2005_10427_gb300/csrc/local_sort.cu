@@ -422,6 +422,10 @@ cudaError_t launch_ls_cap(const Cols& c, const PassList& pl, const int* seg_star
 
 }  // namespace
 
+cudaError_t debug_words_local_sort(unsigned long long limit_ns, int stall) {
+  return set_debug_words(limit_ns, stall);
+}
+
 // The bucket capacity the sort runs with: the largest power of two in
 // [1024, want] whose staged rows leave room for two blocks per SM (the
 // loads of one block overlap the ranking of the other), else the largest

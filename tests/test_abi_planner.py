@@ -251,3 +251,24 @@ def test_tuner_workspace_bound_covers_every_candidate(L):
                              dict(local_capacity=4096, chunk_tiles=4)]:
                     p = qsd.Plan(dims, sigma, top_k=k, global_groups=gg, **opts)
                     assert p.workspace_bytes(nnz) <= need.value, (sigma, k, gg, opts, nnz)
+
+
+def test_noalloc_refuses_while_the_profiler_is_on(L):
+    # the launch profiler allocates pinned memory and events of its own, so
+    # the allocation-free call refuses to run under it, before any device
+    # work (the device pointers here are never dereferenced)
+    p = qsd.Plan([4, 4, 4], [2, 1, 0])
+    c = _capi.Coords()
+    c.buf[0], c.buf[1] = 1 << 36, 2 << 36
+    c.stride = 100
+    assert L.qsd_profile_enable(1) == 0
+    try:
+        assert L.qsd_transpose_noalloc(ctypes.byref(c), None, 100, p.handle, None) == 2
+    finally:
+        assert L.qsd_profile_enable(0) == 0
+
+
+def test_debug_controls_check_arguments_before_device_work(L):
+    assert L.qsd_debug_set_stall(2) == 1
+    assert L.qsd_debug_set_stall(-1) == 1
+    assert L.qsd_debug_set_spin_limit_ns(61 * 10**9) == 1
