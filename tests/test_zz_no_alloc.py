@@ -28,21 +28,43 @@ def qsd():
     return q
 
 
-def _run_ws(qsd, coords, vals, plan, n):
+def _buffers(coords, vals):
     cb = [torch.from_numpy(coords).cuda(), torch.empty_like(torch.from_numpy(coords)).cuda()]
-    vb = [torch.from_numpy(vals).cuda(), torch.empty(n, dtype=torch.float32, device="cuda")]
+    if vals is None:
+        return cb, None
+    vb = [torch.from_numpy(vals).cuda(), torch.empty_like(torch.from_numpy(vals)).cuda()]
+    return cb, vb
+
+
+def _host(cb, vb, sel):
+    return cb[sel].cpu().numpy(), (None if vb is None else vb[sel].cpu().numpy())
+
+
+def _run_ws(qsd, coords, vals, plan, n):
+    cb, vb = _buffers(coords, vals)
     ws = torch.empty(plan.workspace_bytes(n), dtype=torch.uint8, device="cuda")
     sel = qsd.transpose_buffers(cb, vb, 0, n, plan, ws)
-    return cb[sel].cpu().numpy(), vb[sel].cpu().numpy()
+    torch.cuda.synchronize()
+    assert qsd.workspace_status(ws) == 0
+    return _host(cb, vb, sel)
 
 
 def _run_noalloc(qsd, coords, vals, plan, n):
-    cb = [torch.from_numpy(coords).cuda(), torch.empty_like(torch.from_numpy(coords)).cuda()]
-    vb = [torch.from_numpy(vals).cuda(), torch.empty(n, dtype=torch.float32, device="cuda")]
+    cb, vb = _buffers(coords, vals)
     sel = qsd.transpose_noalloc(cb, vb, 0, n, plan)
     torch.cuda.synchronize()
     assert qsd.get_async_status() == 0
-    return cb[sel].cpu().numpy(), vb[sel].cpu().numpy()
+    return _host(cb, vb, sel)
+
+
+def _same(got, want):
+    (gc, gv), (wc, wv) = got, want
+    if not np.array_equal(gc, wc):
+        return False
+    if wv is None:
+        return gv is None
+    bits = np.uint64 if wv.dtype.itemsize == 8 else np.uint32
+    return np.array_equal(gv.view(bits), wv.view(bits))
 
 
 def test_noalloc_matches_workspace_entry_point_twice(qsd):
@@ -52,11 +74,49 @@ def test_noalloc_matches_workspace_entry_point_twice(qsd):
     for sigma in [(0, 2, 1), (2, 1, 0), (1, 0, 2)]:
         plan = qsd.Plan(t.dims, sigma)
         assert plan.workspace_bytes(n) <= 64 << 20
-        want_c, want_v = _run_ws(qsd, coords, vals, plan, n)
+        want = _run_ws(qsd, coords, vals, plan, n)
         for _ in range(2):  # the shared scratch keeps the last call's contents
-            got_c, got_v = _run_noalloc(qsd, coords, vals, plan, n)
-            assert np.array_equal(got_c, want_c), sigma
-            assert np.array_equal(got_v.view(np.uint32), want_v.view(np.uint32)), sigma
+            assert _same(_run_noalloc(qsd, coords, vals, plan, n), want), sigma
+
+
+@pytest.mark.parametrize("case", ["f64", "coords_only", "order4"])
+def test_noalloc_value_widths_and_orders(qsd, case):
+    if case == "order4":
+        t = synth.gen_coo([900, 300, 400, 50], 300_000, [("zipf", 1.2)] * 3 + [("uniform",)],
+                          "f64_normal", seed=13)
+        sigmas = [(0, 1, 3, 2), (3, 2, 1, 0), (1, 0, 2, 3)]
+    else:
+        t = synth.gen_coo([2000, 800, 600], 300_000, [("zipf", 1.1)] * 3,
+                          "f64_uniform" if case == "f64" else "f32_normal", seed=14)
+        sigmas = [(0, 2, 1), (2, 0, 1), (1, 2, 0)]
+    coords = t.coords.numpy()
+    vals = None if case == "coords_only" else t.vals.numpy()
+    n = coords.shape[1]
+    for sigma in sigmas:
+        plan = qsd.Plan(t.dims, sigma)
+        want = _run_ws(qsd, coords, vals, plan, n)
+        for _ in range(2):
+            assert _same(_run_noalloc(qsd, coords, vals, plan, n), want), (case, sigma)
+
+
+def test_noalloc_near_its_scratch_limit(qsd):
+    # the largest bucketed request whose workspace still fits the 64 MiB array
+    dims = [20000, 9000, 28000]
+    plan = qsd.Plan(dims, (0, 2, 1))
+    lo, hi = 1_000_000, 40_000_000
+    while hi - lo > 1000:
+        mid = (lo + hi) // 2
+        if plan.workspace_bytes(mid) <= 64 << 20:
+            lo = mid
+        else:
+            hi = mid
+    n = lo
+    assert plan.workspace_bytes(n) <= 64 << 20 < plan.workspace_bytes(n + 2000)
+    t = synth.gen_coo(dims, n, [("zipf", 1.1)] * 3, "f32_normal", seed=15, device="cuda")
+    coords, vals = t.coords.cpu().numpy(), t.vals.cpu().numpy()
+    want = _run_ws(qsd, coords, vals, plan, n)
+    for _ in range(2):
+        assert _same(_run_noalloc(qsd, coords, vals, plan, n), want)
 
 
 def test_noalloc_rejects_requests_beyond_its_scratch(qsd):
