@@ -175,16 +175,16 @@ def cpu_method_rate(t_coords: np.ndarray, t_vals: np.ndarray, dims, perms, targe
     """The paper's own CPU method (Algorithms 1-3 as counting sorts, parallel
     as its Section 3.2 describes; OpenMP on all host cores) on a strided
     sample of the workload, sized to about target_s seconds."""
-    import oracle
+    import cpu_method
     n_total = t_coords.shape[1]
-    threads = oracle.cpu_method_threads()
+    threads = cpu_method.threads()
 
     def run(m, top_k=0):
         idx = np.linspace(0, n_total - 1, m).astype(np.int64)
         c, v = np.ascontiguousarray(t_coords[:, idx]), np.ascontiguousarray(t_vals[idx])
         t0 = time.perf_counter()
         for sigma in perms:
-            oracle.cpu_method_transpose(c, v, dims, sigma, top_k=top_k)
+            cpu_method.transpose(c, v, dims, sigma, top_k=top_k)
         return time.perf_counter() - t0
 
     m = min(n_total, 1_000_000)
@@ -246,7 +246,7 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="qsd", choices=["qsd", "reference"])
-    ap.add_argument("--workload", default="nell2like", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="deliciouslike", choices=sorted(WORKLOADS))
     ap.add_argument("--nnz", type=int, default=0, help="override the entry count")
     ap.add_argument("--perms", default="", help="comma-separated subset, e.g. 021,102")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -260,7 +260,12 @@ def main():
                     help="timed runs of the batched workload (default: steps, 5..20)")
     ap.add_argument("--no-csf", action="store_true", help="skip the CSF-levels measurement")
     ap.add_argument("--no-topk", action="store_true",
-                    help="skip the Quesadilla vs Top-K-sadilla comparison")
+                    help="skip Top-K-sadilla in the per-order table")
+    ap.add_argument("--no-orders", action="store_true",
+                    help="skip the per-order table (times, roofline fractions, no-skip ablation)")
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the per-order tables of the other single-tensor workloads and "
+                         "the 1M-entry latency")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the Poisson-stream serving measurement")
     args = ap.parse_args()
@@ -410,7 +415,18 @@ def main():
                "d2h_bytes_per_step": len(plans) * nnz * R, "streams": 2}
 
     csf = bench_csf(qsd, t, plans, perms, cb, vbuf, ws, stream) if not args.no_csf else None
-    topk = bench_topk(qsd, wl["dims"], t, perms, cb, vbuf, ws, stream) if not args.no_topk else None
+    orders = None
+    if not args.no_orders:
+        orders = bench_orders(qsd, wl["dims"], t, perms, cb, vbuf, ws, stream,
+                              topk=not args.no_topk)
+    others = None
+    if not args.no_others and rank == 0:
+        others = {}
+        for name, w in WORKLOADS.items():
+            if w["name"] == wl["name"] or name == "uniform3d":
+                continue
+            others[name] = bench_other_workload(qsd, w, dev, stream)
+        others["uniform3d_latency"] = bench_latency(qsd, synth.WORKLOAD_3D_UNIFORM, dev, stream)
 
     batched = None
     if not args.no_batched:
@@ -450,7 +466,9 @@ def main():
                            "perms": [list(p) for p in perms], "input_order": list(range(r)),
                            "out_of_place": True, "parallelism": f"replicas{world}",
                            "l2": "inputs (%.2f GB) larger than L2; no flush" % (nnz * R / 1e9)},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline,
+                "min_traffic_frac": roofline["whole_step_frac"],
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(round(launches_per_step * args.steps)),
                 "launches_per_step": launches_per_step,
                 "kernels": {k: {"launches": a["launches"], "ms": round(a["ms"], 3),
@@ -461,8 +479,10 @@ def main():
             line["cpu_method"] = cpu_method
         if csf is not None:
             line["csf"] = csf
-        if topk is not None:
-            line["topk"] = topk
+        if orders is not None:
+            line["per_order"] = orders
+        if others is not None:
+            line["other_workloads"] = others
         if batched is not None:
             line["batched"] = batched
         if serving is not None:
@@ -550,37 +570,14 @@ def bench_batched(qsd, dev, stream, steps: int, warmup: int, tune: bool = True):
             "tuned_options": tuned, "tune_seconds": None if tune_s is None else round(tune_s, 2)}
 
 
-def bench_serving(qsd, dev, budget_gb: float = 40.0, n_requests: int = 10_000,
-                  rate: float = 2000.0, check_every: int = 200):
-    """The serving workload: a resident pool of 64 tensors (orders 3-4,
-    log-uniform sizes in [1e4, 5e7], Zipf 1.2, float64 values) and 10k
-    requests arriving as a Poisson stream at 2k/s, each a random non-identity
-    target order of a random pool tensor, served under a 40 GB budget by the
-    continuous-batching server. Latency = arrival to completion on the device.
-    Every check_every-th result is compared bit for bit with the standalone
-    transposition of the same request (alone vs in the mix)."""
-    pool_desc, reqs = synth.serving_workload(n_requests=n_requests, rate=rate)
-    t0 = time.perf_counter()
-    pool = [synth.gen_coo(d["dims"], d["nnz"], d["dists"], d["val_kind"], d["seed"], dev)
-            for d in pool_desc]
-    torch.cuda.synchronize()
-    gen_s = time.perf_counter() - t0
-    srv = qsd.Server(int(budget_gb * (1 << 30)), val_bytes=8, streams=2, max_batch=256)
-    ids = [srv.add_tensor(t.coords, t.vals, t.dims) for t in pool]
-    # warm-up: a few requests per order (plans, code paths), not timed
-    for i in range(min(8, len(pool))):
-        srv.submit(ids[i], list(reversed(range(pool[i].order))))
-    warm = 0
-    while warm < min(8, len(pool)):
-        for r in srv.poll(64, wait_ms=100):
-            srv.release(r["request"])
-            warm += 1
-    clock = qsd.server_clock
-    start = clock() + 0.05
-    lat, entries, done_t, first_arrival = [], 0, [], None
-    kept = {}
+def _serve(qsd, srv, ids, pool, reqs, start, check_every, rid_clock):
+    """Submits reqs (arrival offsets from `start`) from a driver thread, polls
+    the results and keeps every check_every-th one. Returns (latencies,
+    completion times, entries, kept results, errors)."""
+    lat, done_t, kept, errors = [], [], {}, []
+    entries = 0
     rid_of = {}
-    errors = []
+    clock = rid_clock
 
     def driver():
         for k, (off, i, perm) in enumerate(reqs):
@@ -595,6 +592,7 @@ def bench_serving(qsd, dev, budget_gb: float = 40.0, n_requests: int = 10_000,
     th = threading.Thread(target=driver)
     th.start()
     got = 0
+    t0 = time.perf_counter()
     while got < len(reqs):
         for r in srv.poll(512, wait_ms=20):
             got += 1
@@ -620,29 +618,135 @@ def bench_serving(qsd, dev, budget_gb: float = 40.0, n_requests: int = 10_000,
             break
     th.join()
     torch.cuda.synchronize()
-    stats = srv.stats()
-    srv.close()
-    same = True
-    for k, (oc, ov) in kept.items():
-        _, i, perm = reqs[k]
-        c, v = qsd.transpose(pool[i].coords.clone(), pool[i].vals.clone(),
-                             qsd.Plan(pool[i].dims, perm))
-        same &= bool(torch.equal(c, oc) and torch.equal(v.view(torch.int64), ov.view(torch.int64)))
+    return lat, done_t, entries, kept, errors
+
+
+def _lat_stats(lat, done_t, start, entries):
     lat_ms = np.array(lat) * 1e3
     span = max(done_t) - start if done_t else float("nan")
-    offered = sum(pool_desc[i]["nnz"] for _, i, _ in reqs) / reqs[-1][0] / 1e9
-    return {"workload": "serve10k_poisson2000_pool64_r3-4_nnz1e4-5e7_zipf1.2_f64",
-            "requests": len(reqs), "completed": len(lat), "errors": len(errors),
-            "budget_gb": budget_gb, "offered_gnnz_s": round(offered, 3),
-            "value": round(entries / span / 1e9, 3), "unit": "Gnnz/s",
+    return {"value": round(entries / span / 1e9, 3), "unit": "Gnnz/s",
+            "seconds": round(span, 3),
             "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
             "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
-            "mean_ms": round(float(lat_ms.mean()), 3), "max_ms": round(float(lat_ms.max()), 3),
-            "steps": stats["steps"], "mean_batch": round(stats["admitted"] / max(stats["steps"], 1), 2),
-            "max_queue_depth": stats["max_queue_depth"],
-            "max_inflight": stats["max_inflight_seen"],
-            "peak_budget_gb": round(stats["peak_bytes"] / (1 << 30), 3),
-            "alone_vs_mix_checked": len(kept), "alone_vs_mix_identical": bool(same),
+            "mean_ms": round(float(lat_ms.mean()), 3), "max_ms": round(float(lat_ms.max()), 3)}
+
+
+def bench_serving(qsd, dev, budget_gb: float = 40.0, n_requests: int = 10_000,
+                  rate: float = 2000.0, check_every: int = 200):
+    """The serving workload: a resident pool of 64 tensors (orders 3-4,
+    log-uniform sizes in [1e4, 5e7], Zipf 1.2, float64 values) and 10k
+    requests, each a random non-identity target order of a random pool
+    tensor, served under a 40 GB budget by the continuous-batching server.
+    Latency = arrival to completion on the device.
+
+    Three arms over the same request list:
+      poisson      arrivals as a Poisson stream at 2k/s (the offered load);
+      saturated    every request queued at once, so the server runs at its
+                   capacity (continuous batching with full steps);
+      single_calls the requests as back-to-back out-of-place single calls on
+                   one stream (the same plans, one call each).
+    Every check_every-th result of both served arms is compared bit for bit
+    with the single call's result for that request (alone vs in the mix)."""
+    pool_desc, reqs = synth.serving_workload(n_requests=n_requests, rate=rate)
+    t0 = time.perf_counter()
+    pool = [synth.gen_coo(d["dims"], d["nnz"], d["dists"], d["val_kind"], d["seed"], dev)
+            for d in pool_desc]
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    clock = qsd.server_clock
+
+    def new_server():
+        srv = qsd.Server(int(budget_gb * (1 << 30)), val_bytes=8, streams=2, max_batch=256)
+        ids = [srv.add_tensor(t.coords, t.vals, t.dims) for t in pool]
+        # warm-up: a few requests per order (plans, code paths), not timed
+        for i in range(min(8, len(pool))):
+            srv.submit(ids[i], list(reversed(range(pool[i].order))))
+        warm = 0
+        while warm < min(8, len(pool)):
+            for r in srv.poll(64, wait_ms=100):
+                srv.release(r["request"])
+                warm += 1
+        return srv, ids
+
+    arms = {}
+    kept_all = {}
+    for arm in ("poisson", "saturated"):
+        srv, ids = new_server()
+        arm_reqs = reqs if arm == "poisson" else [(0.0, i, perm) for _, i, perm in reqs]
+        start = clock() + 0.05
+        lat, done_t, entries, kept, errors = _serve(qsd, srv, ids, pool, arm_reqs, start,
+                                                    check_every, clock)
+        stats = srv.stats()
+        srv.close()
+        a = _lat_stats(lat, done_t, start, entries)
+        a.update({"completed": len(lat), "errors": len(errors), "steps": stats["steps"],
+                  "mean_batch": round(stats["admitted"] / max(stats["steps"], 1), 2),
+                  "max_queue_depth": stats["max_queue_depth"],
+                  "max_inflight": stats["max_inflight_seen"],
+                  "peak_budget_gb": round(stats["peak_bytes"] / (1 << 30), 3)})
+        arms[arm] = a
+        kept_all[arm] = kept
+        del kept
+
+    # the same requests as back-to-back single calls, CUDA events around all
+    plans = {}
+    for _, i, perm in reqs:
+        if (i, perm) not in plans:
+            plans[(i, perm)] = qsd.Plan(pool[i].dims, perm)
+    nmax = max(t.nnz for t in pool)
+    rmax = max(t.order for t in pool)
+    cbuf = [torch.empty((rmax, nmax), dtype=torch.int32, device=dev) for _ in range(2)]
+    vbuf = [torch.empty(nmax, dtype=torch.float64, device=dev) for _ in range(2)]
+    ws = torch.empty(max(p.workspace_bytes(pool[i].nnz) for (i, _), p in plans.items()),
+                     dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    views = {}
+    for t in pool:
+        key = (t.order, t.nnz)
+        if key not in views:
+            views[key] = ([c[:t.order, :t.nnz] for c in cbuf], [v[:t.nnz] for v in vbuf])
+
+    def single(k):
+        _, i, perm = reqs[k]
+        t = pool[i]
+        cb, vb = views[(t.order, t.nnz)]
+        return qsd.transpose_from(t.coords, t.vals, cb, vb, t.nnz, plans[(i, perm)], ws, stream)
+
+    for k in range(min(16, len(reqs))):
+        single(k)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(len(reqs)):
+        single(k)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if qsd.workspace_status(ws, stream) != 0:
+        raise SystemExit("device status set by the single-call arm")
+    ms_single = ev0.elapsed_time(ev1)
+    total_entries = sum(pool[i].nnz for _, i, _ in reqs)
+    arms["single_calls"] = {"value": round(total_entries / (ms_single / 1e3) / 1e9, 3),
+                            "unit": "Gnnz/s", "seconds": round(ms_single / 1e3, 3)}
+
+    # alone vs in the mix: the single call's result for each kept request
+    same = True
+    checked = 0
+    for arm, kept in kept_all.items():
+        for k, (oc, ov) in kept.items():
+            t = pool[reqs[k][1]]
+            sel = single(k)
+            cb, vb = views[(t.order, t.nnz)]
+            same &= bool(torch.equal(cb[sel], oc) and
+                         torch.equal(vb[sel].view(torch.int64), ov.view(torch.int64)))
+            checked += 1
+    offered = total_entries / reqs[-1][0] / 1e9
+    return {"workload": "serve10k_poisson2000_pool64_r3-4_nnz1e4-5e7_zipf1.2_f64",
+            "requests": len(reqs), "budget_gb": budget_gb, "offered_gnnz_s": round(offered, 3),
+            **{k: v for k, v in arms["poisson"].items()},
+            "saturated": arms["saturated"], "single_calls": arms["single_calls"],
+            "saturated_vs_single_calls": round(arms["saturated"]["value"] /
+                                               arms["single_calls"]["value"], 3),
+            "alone_vs_mix_checked": checked, "alone_vs_mix_identical": bool(same),
             "pool_gen_seconds": round(gen_s, 1)}
 
 
@@ -679,33 +783,117 @@ def bench_csf(qsd, t, plans, perms, cb, vbuf, ws, stream, reps: int = 5):
             "per_order": per}
 
 
-def bench_topk(qsd, dims, t, perms, cb, vbuf, ws, stream, reps: int = 5):
-    """Quesadilla (K = 0) against Top-K-sadilla (Section 3.6) for every K an
-    order allows (1 .. r - 2) on each target order: device time per single
-    out-of-place call, and the groups each plan runs (prefix, key modes)."""
-    r, nnz = t.coords.shape
-    dev = t.coords.device
+def _time_calls(qsd, plan, t, cb, vbuf, ws, stream, reps: int, warm: int = 2) -> float:
+    """Mean device time (ms) of one out-of-place call, CUDA events on the
+    launching stream around `reps` back-to-back calls after `warm` calls."""
+    nnz = t.coords.shape[1]
+    need = plan.workspace_bytes(nnz)
+    w = ws if need <= ws.numel() else torch.empty(need, dtype=torch.uint8, device=ws.device)
+    for _ in range(warm):
+        qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, plan, w, stream)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(reps):
+        qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, plan, w, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if qsd.workspace_status(w, stream) != 0:
+        raise SystemExit("device status set in the per-order timing")
+    return ev0.elapsed_time(ev1) / reps
+
+
+def _groups(plan):
+    return [["".join(map(str, g["prefix"])), "".join(map(str, g["keys"])), g["passes"]]
+            for g in plan.info()["groups"]]
+
+
+def bench_orders(qsd, dims, t, perms, cb, vbuf, ws, stream, reps: int = 5, topk: bool = True):
+    """Per target order: device time of one out-of-place call, Gnnz/s and the
+    whole transposition's fraction of the minimum-traffic roofline (one read
+    and one write of every coordinate and value, 2 R bytes per entry, against
+    the measured copy bandwidth); the same for the no-skip plan (a full LSD
+    radix sort over every mode on the same kernels: the baseline whose passes
+    Algorithm 3 skips) and, for every K an order allows, Top-K-sadilla."""
+    r, nnz = t.coords.shape
+    R = 4 * r + t.vals.element_size()
+    peak, _ = measured_peaks()
     per = {}
+    tot_q = tot_ns = 0.0
     for sigma in perms:
         row = {}
-        for K in range(0, max(r - 1, 1)):
-            p = qsd.Plan(dims, sigma, top_k=K)
-            need = p.workspace_bytes(nnz)
-            w = ws if need <= ws.numel() else torch.empty(need, dtype=torch.uint8, device=dev)
-            for _ in range(2):
-                qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, p, w, stream)
-            ev0.record(stream)
-            for _ in range(reps):
-                qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, p, w, stream)
-            ev1.record(stream)
-            torch.cuda.synchronize()
-            ms = ev0.elapsed_time(ev1) / reps
-            row[f"K{K}"] = {"ms": round(ms, 4), "gnnz_s": round(nnz / (ms / 1e3) / 1e9, 2),
-                            "groups": [["".join(map(str, g["prefix"])), "".join(map(str, g["keys"]))]
-                                       for g in p.info()["groups"]]}
+        for label, kw in [("quesadilla", {}), ("no_skip", {"no_skip": True})] + (
+                [(f"topk{K}", {"top_k": K}) for K in range(1, r - 1)] if topk else []):
+            p = qsd.Plan(dims, sigma, **kw)
+            ms = _time_calls(qsd, p, t, cb, vbuf, ws, stream, reps)
+            row[label] = {"ms": round(ms, 4), "gnnz_s": round(nnz / (ms / 1e3) / 1e9, 2),
+                          "whole_transpose_frac": round(2 * R * nnz / (ms / 1e3) / 1e9 / peak, 4),
+                          "groups": _groups(p)}
+        tot_q += row["quesadilla"]["ms"]
+        tot_ns += row["no_skip"]["ms"]
         per["".join(map(str, sigma))] = row
-    return {"what": "single calls: Quesadilla (K0) and Top-K-sadilla (K >= 1)", "per_order": per}
+    return {"what": "single out-of-place calls per target order; whole_transpose_frac = "
+                    "2*R*nnz / time / measured copy bandwidth; no_skip = full LSD radix sort "
+                    "over every mode on the same kernels; topkK = Top-K-sadilla",
+            "bytes_per_entry_min": 2 * R,
+            "sum_ms": {"quesadilla": round(tot_q, 3), "no_skip": round(tot_ns, 3)},
+            "skipping_speedup": round(tot_ns / tot_q, 3) if tot_q else None,
+            "per_order": per}
+
+
+def bench_other_workload(qsd, wl, dev, stream, reps: int = 5):
+    """Another single-tensor workload's per-order table (generated on the
+    device, timed like the line's own orders, then freed)."""
+    t = synth.make(wl, device=dev)
+    r, nnz = t.coords.shape
+    plans = [qsd.Plan(wl["dims"], s) for s in wl["perms"]]
+    ws = torch.empty(max(max(p.workspace_bytes(nnz) for p in plans),
+                         max(qsd.Plan(wl["dims"], s, no_skip=True).workspace_bytes(nnz)
+                             for s in wl["perms"])), dtype=torch.uint8, device=dev)
+    cb = [torch.empty((r, nnz), dtype=torch.int32, device=dev) for _ in range(2)]
+    vbuf = [torch.empty(nnz, dtype=t.vals.dtype, device=dev) for _ in range(2)]
+    out = bench_orders(qsd, wl["dims"], t, wl["perms"], cb, vbuf, ws, stream, reps=reps,
+                       topk=False)
+    tot = out["sum_ms"]["quesadilla"]
+    R = 4 * r + t.vals.element_size()
+    peak, _ = measured_peaks()
+    out["workload"] = wl["name"]
+    out["value"] = round(len(plans) * nnz / (tot / 1e3) / 1e9, 3)
+    out["unit"] = "Gnnz/s"
+    out["whole_step_frac"] = round(2 * R * nnz * len(plans) / (tot / 1e3) / 1e9 / peak, 4)
+    del t, cb, vbuf, ws
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_latency(qsd, wl, dev, stream, calls: int = 50):
+    """Latency of one single out-of-place call on a small tensor (1M entries
+    fit the L2 cache, so this measures launch and latency, not bandwidth):
+    CUDA events around every call, min and median."""
+    t = synth.make(wl, device=dev)
+    r, nnz = t.coords.shape
+    out = {"workload": wl["name"]}
+    for sigma in wl["perms"]:
+        p = qsd.Plan(wl["dims"], sigma)
+        ws = torch.empty(p.workspace_bytes(nnz), dtype=torch.uint8, device=dev)
+        cb = [torch.empty((r, nnz), dtype=torch.int32, device=dev) for _ in range(2)]
+        vbuf = [torch.empty(nnz, dtype=t.vals.dtype, device=dev) for _ in range(2)]
+        for _ in range(5):
+            qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, p, ws, stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(calls)]
+        for a, b in evs:
+            a.record(stream)
+            qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, p, ws, stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        if qsd.workspace_status(ws, stream) != 0:
+            raise SystemExit("device status set in the latency run")
+        us = sorted(a.elapsed_time(b) * 1e3 for a, b in evs)
+        out["".join(map(str, sigma))] = {
+            "min_us": round(us[0], 1), "median_us": round(us[len(us) // 2], 1),
+            "gnnz_s_at_median": round(nnz / (us[len(us) // 2] / 1e6) / 1e9, 2),
+            "groups": _groups(p)}
+    return out
 
 
 def sampled_check(qsd, t, plans, perms, cb, vbuf, ws, stream):
