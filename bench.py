@@ -813,7 +813,8 @@ def bench_orders(qsd, dims, t, perms, cb, vbuf, ws, stream, reps: int = 5, topk:
     and one write of every coordinate and value, 2 R bytes per entry, against
     the measured copy bandwidth); the same for the no-skip plan (a full LSD
     radix sort over every mode on the same kernels: the baseline whose passes
-    Algorithm 3 skips) and, for every K an order allows, Top-K-sadilla."""
+    Algorithm 3 skips), the (key, index) form where the plan has a group that
+    takes it, and, for every K an order allows, Top-K-sadilla."""
     r, nnz = t.coords.shape
     R = 4 * r + t.vals.element_size()
     peak, _ = measured_peaks()
@@ -821,8 +822,12 @@ def bench_orders(qsd, dims, t, perms, cb, vbuf, ws, stream, reps: int = 5, topk:
     tot_q = tot_ns = 0.0
     for sigma in perms:
         row = {}
-        for label, kw in [("quesadilla", {}), ("no_skip", {"no_skip": True})] + (
-                [(f"topk{K}", {"top_k": K}) for K in range(1, r - 1)] if topk else []):
+        variants = [("quesadilla", {}), ("no_skip", {"no_skip": True})]
+        if any(g["key_index"] for g in qsd.Plan(dims, sigma, key_index=True).info()["groups"]):
+            variants.append(("key_index", {"key_index": True}))
+        if topk:
+            variants += [(f"topk{K}", {"top_k": K}) for K in range(1, r - 1)]
+        for label, kw in variants:
             p = qsd.Plan(dims, sigma, **kw)
             ms = _time_calls(qsd, p, t, cb, vbuf, ws, stream, reps)
             row[label] = {"ms": round(ms, 4), "gnnz_s": round(nnz / (ms / 1e3) / 1e9, 2),
@@ -835,7 +840,10 @@ def bench_orders(qsd, dims, t, perms, cb, vbuf, ws, stream, reps: int = 5, topk:
                     "2*R*nnz / time / measured copy bandwidth; no_skip = full LSD radix sort "
                     "over every mode on the same kernels; topkK = Top-K-sadilla",
             "bytes_per_entry_min": 2 * R,
-            "sum_ms": {"quesadilla": round(tot_q, 3), "no_skip": round(tot_ns, 3)},
+            "sum_ms": {"quesadilla": round(tot_q, 3), "no_skip": round(tot_ns, 3),
+                       "best_of_quesadilla_and_key_index": round(sum(
+                           min(v["quesadilla"]["ms"], v.get("key_index", v["quesadilla"])["ms"])
+                           for v in per.values()), 3)},
             "skipping_speedup": round(tot_ns / tot_q, 3) if tot_q else None,
             "per_order": per}
 
@@ -872,8 +880,8 @@ def bench_latency(qsd, wl, dev, stream, calls: int = 50):
     t = synth.make(wl, device=dev)
     r, nnz = t.coords.shape
     out = {"workload": wl["name"]}
-    for sigma in wl["perms"]:
-        p = qsd.Plan(wl["dims"], sigma)
+    for sigma, kw in [(s, kw) for s in wl["perms"] for kw in ({}, {"key_index": True})]:
+        p = qsd.Plan(wl["dims"], sigma, **kw)
         ws = torch.empty(p.workspace_bytes(nnz), dtype=torch.uint8, device=dev)
         cb = [torch.empty((r, nnz), dtype=torch.int32, device=dev) for _ in range(2)]
         vbuf = [torch.empty(nnz, dtype=t.vals.dtype, device=dev) for _ in range(2)]
@@ -889,7 +897,7 @@ def bench_latency(qsd, wl, dev, stream, calls: int = 50):
         if qsd.workspace_status(ws, stream) != 0:
             raise SystemExit("device status set in the latency run")
         us = sorted(a.elapsed_time(b) * 1e3 for a, b in evs)
-        out["".join(map(str, sigma))] = {
+        out["".join(map(str, sigma)) + ("_key_index" if kw else "")] = {
             "min_us": round(us[0], 1), "median_us": round(us[len(us) // 2], 1),
             "gnnz_s_at_median": round(nnz / (us[len(us) // 2] / 1e6) / 1e9, 2),
             "groups": _groups(p)}

@@ -111,6 +111,15 @@ typedef struct {
                             the same result. 0, or K >= order - 1: plain
                             Quesadilla; ignored under no_skip.
                             0 <= K <= QSD_MAX_ORDER */
+  int key_index;         /* nonzero: every group without a prefix whose key
+                            fits 64 bits and takes two or more digit passes
+                            sorts (packed key, entry index) pairs instead of
+                            whole entries, and moves the coordinates and the
+                            values once at the end, gathered through the
+                            final index (Algorithm 2's perm array); the same
+                            result, fewer bytes per pass, one random read of
+                            every entry. Needs 8 (key <= 32 bits) or 12 bytes
+                            per entry more workspace */
 } qsd_plan_options;
 
 /* Description of a plan (qsd_plan_get_info). */
@@ -137,6 +146,8 @@ typedef struct {
   int group_key_bits[QSD_MAX_ORDER];
   int group_digit_passes[QSD_MAX_ORDER];
   int local_capacity;
+  /* 1 where group g runs in (key, index) form (qsd_plan_options.key_index) */
+  int group_key_index[QSD_MAX_ORDER];
 } qsd_plan_info;
 
 /* Builds the plan for transposing an order-`order` tensor with the given

@@ -61,7 +61,8 @@ class Plan:
                  input_mode_order: Optional[Sequence[int]] = None, *,
                  validate: bool = False, digit_bits: int = 0,
                  local_capacity: int = 0, no_skip: bool = False, tile: int = 0,
-                 chunk_tiles: int = 0, global_groups: bool = False, top_k: int = 0):
+                 chunk_tiles: int = 0, global_groups: bool = False, top_k: int = 0,
+                 key_index: bool = False):
         L = lib()
         r = len(dims)
         self.dims = [int(d) for d in dims]
@@ -71,11 +72,12 @@ class Plan:
             [int(x) for x in input_mode_order]
         opts = _capi.PlanOptions(int(bool(validate)), int(digit_bits), int(local_capacity),
                                  int(bool(no_skip)), int(tile), int(chunk_tiles),
-                                 int(bool(global_groups)), int(top_k))
+                                 int(bool(global_groups)), int(top_k), int(bool(key_index)))
         self.options = dict(validate=bool(validate), digit_bits=int(digit_bits),
                             local_capacity=int(local_capacity), no_skip=bool(no_skip),
                             tile=int(tile), chunk_tiles=int(chunk_tiles),
-                            global_groups=bool(global_groups), top_k=int(top_k))
+                            global_groups=bool(global_groups), top_k=int(top_k),
+                            key_index=bool(key_index))
         handle = ctypes.c_void_p()
         dims_arr = (ctypes.c_int64 * max(r, 1))(*self.dims)
         st = L.qsd_plan_ex(r, dims_arr, _i32(self.input_mode_order) if r else None,
@@ -107,7 +109,8 @@ class Plan:
             pl, nk = inf.group_prefix_len[g], inf.group_num_keys[g]
             groups.append(dict(prefix=tuple(sig[:pl]), keys=tuple(sig[pl:pl + nk]),
                                key_bits=int(inf.group_key_bits[g]),
-                               passes=int(inf.group_digit_passes[g])))
+                               passes=int(inf.group_digit_passes[g]),
+                               key_index=bool(inf.group_key_index[g])))
         return dict(order=r, input_mode_order=list(inf.input_mode_order[:r]),
                     target_perm=sig, calls=calls, num_calls=inf.num_calls,
                     num_bucketed_calls=inf.num_bucketed_calls, groups=groups,
@@ -339,7 +342,8 @@ def tune_plan(plan: "Plan", in_coords, in_vals, reps: int = 3, stream=None):
                  validate=bool(opts["validate"]), digit_bits=opts["digit_bits"],
                  local_capacity=opts["local_capacity"], no_skip=bool(opts["no_skip"]),
                  tile=opts["tile"], chunk_tiles=opts["chunk_tiles"],
-                 global_groups=bool(opts["global_groups"]), top_k=opts["top_k"])
+                 global_groups=bool(opts["global_groups"]), top_k=opts["top_k"],
+                 key_index=bool(opts["key_index"]))
     return tuned, float(ms.value), opts
 
 

@@ -29,7 +29,8 @@ class PlanOptions(ctypes.Structure):
     _fields_ = [("validate", ctypes.c_int), ("digit_bits", ctypes.c_int),
                 ("local_capacity", ctypes.c_int), ("no_skip", ctypes.c_int),
                 ("tile", ctypes.c_int), ("chunk_tiles", ctypes.c_int),
-                ("global_groups", ctypes.c_int), ("top_k", ctypes.c_int)]
+                ("global_groups", ctypes.c_int), ("top_k", ctypes.c_int),
+                ("key_index", ctypes.c_int)]
 
 
 _A = ctypes.c_int * MAX_ORDER
@@ -40,7 +41,8 @@ class PlanInfo(ctypes.Structure):
                 ("num_calls", ctypes.c_int), ("num_bucketed_calls", ctypes.c_int),
                 ("call_prefix_len", _A), ("call_mode", _A), ("num_groups", ctypes.c_int),
                 ("group_prefix_len", _A), ("group_num_keys", _A), ("group_key_bits", _A),
-                ("group_digit_passes", _A), ("local_capacity", ctypes.c_int)]
+                ("group_digit_passes", _A), ("local_capacity", ctypes.c_int),
+                ("group_key_index", _A)]
 
 
 class ProfileRecord(ctypes.Structure):

@@ -515,7 +515,7 @@ qsd_status check_batch_items(const qsd_batch_item* items, int n, int val_bytes) 
 
 void fill_batch_tensor(BatchTensor& t, const qsd_batch_item& it) {
   t.plan = *it.plan;
-  t.base_opts = it.plan->opts;
+  t.base_opts = it.plan->opts;  // batches sort whole entries (no (key, index) form)
   t.nnz = it.nnz;
   t.in = it.in;
   t.in_stride = it.in_stride;

@@ -34,9 +34,13 @@ size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
   size_t status, counters, seg_start, seg_lb, large, chunk_base, group_base, chunk_owner,
-      group_owner, chunk_hist, group_sum, total;
+      group_owner, chunk_hist, group_sum, keyrows, total;
   int max_large, max_chunks, max_groups, max_passes;
+  int64_t key_stride;  // elements per (key, index) row: nnz rounded up to 4
 };
+
+// Rows of a group in (key, index) form: its key words and the index.
+int key_rows(const Group& g) { return g.key_words + 1; }
 
 bool plan_has_prefix_group(const qsd_plan_s* p) {
   for (int g = 0; g < p->ngroups; ++g)
@@ -56,6 +60,15 @@ Layout layout_for(const qsd_plan_s* p, int64_t nnz, int vbytes) {
   const bool segs = plan_has_prefix_group(p);
   L.max_large = segs ? (int)(n / (C + 1) + 1) : 1;
   L.max_chunks = (int)((n + CH - 1) / CH + L.max_large);
+  int krows = 0;  // (key, index) groups: rows and their own chunk length
+  for (int g = 0; g < p->ngroups; ++g) {
+    if (!p->groups[g].key_index) continue;
+    const int W = key_rows(p->groups[g]);
+    krows = std::max(krows, W);
+    const int CHk = digit_chunk(W, 0, p->opts.tile, p->opts.chunk_tiles);
+    L.max_chunks = std::max(L.max_chunks, (int)((n + CHk - 1) / CHk + 1));
+  }
+  L.key_stride = (n + 3) & ~int64_t(3);
   L.max_groups = (L.max_chunks + kGroupChunks - 1) / kGroupChunks + L.max_large;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -74,6 +87,8 @@ Layout layout_for(const qsd_plan_s* p, int64_t nnz, int vbytes) {
   L.group_owner = take(segs ? sizeof(int) * (size_t)L.max_groups : 0);
   L.chunk_hist = take(sizeof(uint32_t) * (size_t)L.max_chunks * kRadix);
   L.group_sum = take(sizeof(uint32_t) * (size_t)L.max_passes * L.max_groups * kRadix);
+  // two sets of (key, index) rows the passes alternate between
+  L.keyrows = take(sizeof(int32_t) * 2 * (size_t)krows * (size_t)L.key_stride);
   L.total = off;
   return L;
 }
@@ -197,6 +212,75 @@ qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
     const int P = g.npasses;
     const bool internal = cur.idx >= 0;
 
+    if (g.key_index && nnz > C) {
+      // (key, index) form: pack every entry's key and index into rows, sort
+      // the rows with the group's digit passes, then move the coordinates
+      // and values once, gathered through the sorted index.
+      const int W = key_rows(g);
+      const int64_t ks = L.key_stride;
+      int32_t* krow[2] = {reinterpret_cast<int32_t*>(base + L.keyrows), nullptr};
+      krow[1] = krow[0] + (size_t)W * ks;
+      const int F = internal ? cur.idx ^ 1 : 0;
+      KeyPack kp;
+      std::memset(&kp, 0, sizeof(kp));
+      kp.nkeys = g.nkeys;
+      kp.words = g.key_words;
+      for (int i = 0; i < g.nkeys; ++i) {
+        kp.mode[i] = g.key_modes[i];
+        kp.base[i] = g.kbase[i];
+      }
+      auto kcols = [&](const int32_t* in, const void* vin, int64_t in_stride, int32_t* out,
+                       void* vout, int64_t out_stride, int order, int vbytes) {
+        Cols c;
+        c.in = in;
+        c.vin = vin;
+        c.in_stride = in_stride;
+        c.out = out;
+        c.vout = vout;
+        c.out_stride = out_stride;
+        c.order = order;
+        c.vbytes = vbytes;
+        return c;
+      };
+      QSD_LAUNCH(tag("pack", gi, -1, nnz, 4 * g.nkeys + 4 * W),
+                 launch_pack(kcols(cur.c, nullptr, cur.stride, krow[0], nullptr, ks, plan->order,
+                                   0),
+                             kp, nnz, st));
+      QSD_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * kNumCounters, st));
+      LargeSegs ls;
+      std::memset(&ls, 0, sizeof(ls));
+      ls.single = 1;
+      ls.nnz = nnz;
+      ls.tile = digit_tile(W, 0, plan->opts.tile);
+      ls.chunk = digit_chunk(W, 0, plan->opts.tile, plan->opts.chunk_tiles);
+      ls.counters = counters;
+      const int max_chunks = (nnz + ls.chunk - 1) / ls.chunk;
+      const int max_groups = (max_chunks + kGroupChunks - 1) / kGroupChunks;
+      for (int p = 0; p < P; ++p)
+        QSD_CUDA(cudaMemsetAsync(group_sum + (size_t)p * L.max_groups * kRadix, 0,
+                                 sizeof(uint32_t) * (size_t)max_groups * kRadix, st));
+      for (int p = 0; p < P; ++p) {
+        const Cols kc = kcols(krow[p & 1], nullptr, ks, krow[(p + 1) & 1], nullptr, ks, W, 0);
+        uint32_t* gs = group_sum + (size_t)p * L.max_groups * kRadix;
+        QSD_LAUNCH(tag("chunk_hist", gi, p, nnz, 4 * g.kpass[p].nfields),
+                   launch_chunk_hist(kc, ls, g.kpass[p], chunk_hist, gs,
+                                     counters + kCntClaim + 2 * p, max_chunks, pb1, st));
+        QSD_LAUNCH(tag("chunk_scan", gi, p, nnz, 0),
+                   launch_chunk_scan(ls, chunk_hist, gs, max_groups, pb1, st));
+        QSD_LAUNCH(tag("digit_move", gi, p, nnz, 2 * 4 * W),
+                   launch_digit_move(kc, ls, g.kpass[p], chunk_hist,
+                                     counters + kCntClaim + 2 * p + 1, max_chunks, status, pb1,
+                                     st));
+      }
+      const int32_t* idx = krow[P & 1] + (size_t)g.key_words * ks;
+      QSD_LAUNCH(tag("gather", gi, -1, nnz, 2 * R + 4),
+                 launch_gather(kcols(cur.c, cur.v, cur.stride, coords->buf[F],
+                                     has_vals ? vals->buf[F ^ flipv] : nullptr, coords->stride,
+                                     plan->order, has_vals ? vals->elem_bytes : 0),
+                               idx, nnz, st));
+      cur = buf_src(F);
+      continue;
+    }
     if (g.prefix_len == 0 && nnz <= C) {
       const int F = internal ? cur.idx ^ 1 : 0;
       QSD_LAUNCH(tag("local_sort", gi, -1, nnz, 2 * R),

@@ -188,6 +188,22 @@ size_t csf_workspace_bytes(int order, int nnz);
 // [0, nnz)): a zero-pass plan asked for a distinct output buffer.
 cudaError_t launch_copy(const Cols& c, int nnz, cudaStream_t stream);
 
+// (key, index) form of a group: key mode i (a coordinate row) at bit
+// base[i] of the packed key; `words` key words (1 or 2).
+struct KeyPack {
+  int nkeys;
+  int words;
+  int mode[kMaxOrder];
+  int base[kMaxOrder];
+};
+// Writes the rows c.out + k * c.out_stride (c.out_stride a multiple of 4,
+// c.out 16-byte aligned): k < words the packed key's 32-bit words, k = words
+// the entry index, for entries [0, nnz) of the rows c.in.
+cudaError_t launch_pack(const Cols& c, const KeyPack& kp, int nnz, cudaStream_t stream);
+// out rows / values [j] = in rows / values [idx[j]] for j in [0, nnz); idx
+// is 16-byte aligned.
+cudaError_t launch_gather(const Cols& c, const int32_t* idx, int nnz, cudaStream_t stream);
+
 int seg_lookback_words(int nnz);
 
 // Profiling (qsd_profile_*): when enabled, each launch is bracketed by CUDA

@@ -74,6 +74,40 @@ bool schedule_digits(const int64_t* dims, qsd::Group& g, int digit_bits) {
   return true;
 }
 
+// (key, index) form of a group without a prefix whose packed key fits 64
+// bits and takes two or more passes: the same digit passes, re-expressed on
+// the rows the pack kernel writes (key bits 0..31 in word 0, bits 32..63 in
+// word 1, then the entry index). The plain passes stay for the paths that
+// sort whole entries (a tensor small enough for one block, batches).
+void to_key_index(const int64_t* dims, qsd::Group& g) {
+  if (g.prefix_len != 0 || g.npasses < 2 || g.key_bits > 64) return;
+  int acc = 0;
+  for (int i = g.nkeys - 1; i >= 0; --i) {  // last key mode = lowest bits
+    g.kwidth[i] = mode_bits(dims[g.key_modes[i]]);
+    g.kbase[i] = acc;
+    acc += g.kwidth[i];
+  }
+  g.key_index = 1;
+  g.key_words = g.key_bits > 32 ? 2 : 1;
+  int lo = 0;
+  for (int p = 0; p < g.npasses; ++p) {
+    qsd::PassDesc& d = g.kpass[p];
+    d.bits = g.pass[p].bits;
+    const int hi = lo + d.bits;
+    d.nfields = 0;
+    for (int w = 0; w < 2; ++w) {
+      const int a = std::max(lo, 32 * w), b = std::min(hi, 32 * w + 32);
+      if (a >= b) continue;
+      qsd::DigitField& f = d.f[d.nfields++];
+      f.mode = (int8_t)w;
+      f.shift = (int8_t)(a - 32 * w);
+      f.width = (int8_t)(b - a);
+      f.dst = (int8_t)(a - lo);
+    }
+    lo = hi;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -212,6 +246,8 @@ qsd_status qsd_plan_ex(int order, const int64_t* dims,
       delete p;
       return QSD_ERR_UNSUPPORTED;  // a key too wide for the digit width
     }
+  if (o.key_index)
+    for (int i = 0; i < p->ngroups; ++i) to_key_index(p->dims, p->groups[i]);
   *out = p;
   return QSD_OK;
 }
@@ -241,6 +277,7 @@ qsd_status qsd_plan_get_info(qsd_plan_t plan, qsd_plan_info* info) {
     info->group_num_keys[g] = plan->groups[g].nkeys;
     info->group_key_bits[g] = plan->groups[g].key_bits;
     info->group_digit_passes[g] = plan->groups[g].npasses;
+    info->group_key_index[g] = plan->groups[g].key_index;
   }
   info->local_capacity = plan->local_capacity;
   return QSD_OK;

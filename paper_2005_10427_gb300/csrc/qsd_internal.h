@@ -41,6 +41,15 @@ struct Group {
   int key_bits;
   int npasses;
   PassDesc pass[kMaxPasses];
+  // (key, index) form: the packed key's words and the entry index are the
+  // rows the passes sort; kpass[p] is pass p with its fields naming key
+  // words instead of modes. Key mode i sits at bits [kbase[i], kbase[i] +
+  // kwidth[i]) of the key.
+  int key_index;
+  int key_words;  // 1 (key <= 32 bits) or 2
+  int kbase[kMaxOrder];
+  int kwidth[kMaxOrder];
+  PassDesc kpass[kMaxPasses];
 };
 
 }  // namespace qsd

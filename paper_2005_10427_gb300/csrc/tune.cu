@@ -6,8 +6,9 @@
 // for a K (Section 3.6: fewer calls of Algorithm 3, then one complete sort of
 // the buckets of the first K target modes), whether groups with a prefix
 // sort bucket by bucket or as one global sort by (prefix, key), the radix
-// digit width (how many passes), the tile and chunk sizes, and the bucket
-// capacity of the shared-memory sort.
+// digit width (how many passes), the tile and chunk sizes, the bucket
+// capacity of the shared-memory sort, and whether groups without a prefix
+// sort (key, index) pairs and gather the entries once at the end.
 // Each candidate is timed with CUDA events over real out-of-place
 // transpositions of the caller's data; a coordinate search keeps the fastest.
 #include <cuda_runtime.h>
@@ -32,7 +33,8 @@ bool has_prefix_group(const qsd_plan_s* p) {
 
 // The values each option takes in the search (0 = the library's choice);
 // top_k takes 0 .. order - 2.
-constexpr int kDims = 6;
+constexpr int kDims = 7;
+const int kKeyIndex[] = {0, 1};
 const int kStructure[] = {0, 1};
 const int kDigits[] = {8, 7, 6, 5};
 const int kTiles[] = {0, 4096, 3584, 2048};
@@ -48,6 +50,7 @@ void for_each_candidate_value(int dim, int order, F f) {
     case 3: for (int v : kTiles) f(v); break;
     case 4: for (int v : kCaps) f(v); break;
     case 5: for (int v : kChunks) f(v); break;
+    case 6: for (int v : kKeyIndex) f(v); break;
   }
 }
 
@@ -58,8 +61,19 @@ int& field(qsd_plan_options& o, int dim) {
     case 2: return o.digit_bits;
     case 3: return o.tile;
     case 4: return o.local_capacity;
-    default: return o.chunk_tiles;
+    case 5: return o.chunk_tiles;
+    default: return o.key_index;
   }
+}
+
+// Whether the plan under options o has a group in (key, index) form.
+bool has_key_index_group(const qsd_plan_s* base, const qsd_plan_options& o) {
+  qsd_plan_t p = nullptr;
+  if (plan_with(base, o, &p) != QSD_OK) return false;
+  bool r = false;
+  for (int g = 0; g < p->ngroups; ++g) r |= p->groups[g].key_index != 0;
+  qsd_plan_destroy(p);
+  return r;
 }
 
 // Whether the plan under options o has a group sorted bucket by bucket.
@@ -107,6 +121,8 @@ qsd_status qsd_plan_tune_workspace_bytes(qsd_plan_t plan, int64_t nnz, size_t* b
       c.digit_bits = 5;
       c.chunk_tiles = 1;
       c.tile = 2048;
+      take(c);
+      c.key_index = 1;
       take(c);
     }
   *bytes = best;
@@ -165,6 +181,13 @@ qsd_status qsd_plan_tune(qsd_plan_t plan, const int32_t* in_coords, int64_t in_s
     // the bucket capacity only matters when a bucket sort runs: a group with
     // a prefix, or a whole tensor small enough for one block
     if (dim == 4 && (!prefix || best.global_groups) && nnz > 8192) continue;
+    // the (key, index) form only changes groups without a prefix that take
+    // two or more passes
+    if (dim == 6) {
+      qsd_plan_options k = best;
+      k.key_index = 1;
+      if (!has_key_index_group(plan, k)) continue;
+    }
     qsd_plan_options base = best;
     for_each_candidate_value(dim, plan->order, [&](int v) {
       if (s != QSD_OK || field(base, dim) == v) return;

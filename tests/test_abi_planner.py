@@ -272,3 +272,33 @@ def test_debug_controls_check_arguments_before_device_work(L):
     assert L.qsd_debug_set_stall(2) == 1
     assert L.qsd_debug_set_stall(-1) == 1
     assert L.qsd_debug_set_spin_limit_ns(61 * 10**9) == 1
+
+
+def test_key_index_form_of_groups(L):
+    # only groups without a prefix, keys of at most 64 bits and two or more
+    # digit passes take the (key, index) form; the calls and passes are the
+    # plain plan's
+    cases = [([1000, 1000, 1000], (2, 1, 0), [True]),            # 20-bit key, 3 passes
+             ([12000, 9000, 28000], (0, 2, 1), [False]),          # bucketed
+             ([4800000, 1700000, 1800000, 1100], (1, 2, 3, 0), [True]),   # 53 bits
+             ([4800000, 1700000, 1800000, 1100], (1, 0, 3, 2), [True, False]),
+             ([1 << 20] * 5, (4, 3, 2, 1, 0), [False]),           # 80 bits
+             ([300, 200, 100], (2, 0, 1), [True])]                 # 7-bit key: 1 pass
+    for dims, sigma, want in cases:
+        plain = qsd.Plan(dims, sigma).info()
+        ki = qsd.Plan(dims, sigma, key_index=True).info()
+        assert plain["calls"] == ki["calls"]
+        assert [g["passes"] for g in plain["groups"]] == [g["passes"] for g in ki["groups"]]
+        got = [g["key_index"] for g in ki["groups"]]
+        want = [w and g["passes"] >= 2 for w, g in zip(want, plain["groups"])]
+        assert got == want, (dims, sigma, got)
+        assert not any(g["key_index"] for g in plain["groups"])
+    # two sets of (key, index) rows in the workspace: 8 (<= 32-bit key) or
+    # 12 bytes per entry and set
+    n = 1 << 20
+    p0 = qsd.Plan([1000, 1000, 1000], (2, 1, 0))
+    p1 = qsd.Plan([1000, 1000, 1000], (2, 1, 0), key_index=True)
+    assert p1.workspace_bytes(n) - p0.workspace_bytes(n) >= 2 * 8 * n
+    d3 = [1 << 20] * 3
+    p2 = qsd.Plan(d3, (2, 1, 0), key_index=True)  # 40-bit key: two words
+    assert p2.workspace_bytes(n) - qsd.Plan(d3, (2, 1, 0)).workspace_bytes(n) >= 2 * 12 * n

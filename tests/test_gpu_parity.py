@@ -328,3 +328,61 @@ def test_out_of_place_keeps_input(qsd):
         assert np.array_equal(cb[sel].cpu().numpy(), rc), sigma
         assert np.array_equal(vb[sel].cpu().numpy(), rv), sigma
         assert np.array_equal(ic.cpu().numpy(), coords) and np.array_equal(iv.cpu().numpy(), vals)
+
+
+def _key_index_groups(qsd, dims, sigma, tau=None):
+    return [g["key_index"] for g in qsd.Plan(dims, sigma, input_mode_order=tau,
+                                              key_index=True).info()["groups"]]
+
+
+@pytest.mark.parametrize("r", [2, 3, 4, 5])
+def test_key_index_every_permutation(qsd, r):
+    # groups without a prefix sort (packed key, entry index) rows and gather
+    # the entries once at the end; a small capacity keeps the digit passes in
+    # play at this size
+    dims = [300, 2000, 3000, 40, 9][:r]
+    coords, vals = tensor(dims, 60_000, seed=40 + r, zipf=1.1, dup=0.05)
+    used = 0
+    for sigma in itertools.permutations(range(r)):
+        used += sum(_key_index_groups(qsd, dims, sigma))
+        check(qsd, coords, vals, dims, sigma, key_index=True, local_capacity=1024)
+    assert used > 0
+
+
+@pytest.mark.parametrize("nnz", [1, 3, 4, 5, 4097, 8193, 70001])
+def test_key_index_sizes_and_tails(qsd, nnz):
+    dims = [70, 90, 60]
+    coords, vals = tensor(dims, nnz, seed=nnz + 5, zipf=1.1)
+    for sigma in [(2, 1, 0), (1, 2, 0), (1, 0, 2)]:
+        check(qsd, coords, vals, dims, sigma, key_index=True, local_capacity=1024)
+
+
+@pytest.mark.parametrize("val_kind", ["f32_normal", "f64_uniform", None])
+def test_key_index_value_widths_and_key_words(qsd, val_kind):
+    # 20-, 40- and 60-bit keys: one and two key words; an 80-bit key stays in
+    # whole-entry form
+    for dims, sigma in [([1000, 1000, 1000], (2, 1, 0)),
+                        ([1 << 20, 1 << 20, 1 << 20], (2, 1, 0)),
+                        ([1 << 20] * 4, (3, 2, 1, 0)),
+                        ([1 << 20] * 5, (4, 3, 2, 1, 0))]:
+        coords, vals = tensor(dims, 50_000, seed=sum(dims) % 1000, val_kind=val_kind or
+                              "f32_normal", zipf=1.2)
+        if val_kind is None:
+            vals = None
+        check(qsd, coords, vals, dims, sigma, key_index=True, local_capacity=1024)
+
+
+def test_key_index_duplicates_and_input_orders(qsd):
+    dims = [40, 30, 50, 20]
+    for tau in [None, (2, 0, 3, 1)]:
+        coords, vals = tensor(dims, 40_000, seed=77, zipf=1.0, dup=0.3, tau=tau)
+        for sigma in [(3, 2, 1, 0), (1, 3, 0, 2), (2, 0, 3, 1), (0, 3, 2, 1)]:
+            check(qsd, coords, vals, dims, sigma, tau=tau, key_index=True, local_capacity=1024)
+
+
+def test_key_index_multi_group_plans(qsd):
+    # a global group in (key, index) form followed by bucketed groups
+    dims = [4800, 1700, 1800, 110]
+    coords, vals = tensor(dims, 300_000, seed=91, val_kind="f64_uniform", zipf=1.3)
+    for sigma in [(1, 0, 3, 2), (2, 0, 3, 1), (3, 0, 2, 1), (1, 2, 3, 0), (3, 2, 1, 0)]:
+        check(qsd, coords, vals, dims, sigma, key_index=True)
