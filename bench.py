@@ -751,9 +751,12 @@ def bench_serving(qsd, dev, budget_gb: float = 40.0, n_requests: int = 10_000,
 
 
 def bench_csf(qsd, t, plans, perms, cb, vbuf, ws, stream, reps: int = 5):
-    """CSF levels of each transposed output (qsd_csf_build): device time per
-    build, entries per second, and DRAM-side bytes of the two sweeps (every
-    coordinate row read twice) plus the node arrays written."""
+    """CSF levels of each transposed output. Per order: the transposition
+    alone, the separate CSF build on its result (qsd_csf_build: a count and a
+    write sweep over every coordinate row), and the fused call
+    (qsd_transpose_csf_from_ws: the last movement leaves each entry's first
+    differing level, the CSF pass reads those bytes). Device times, CUDA
+    events; fused_csf_ms = fused - transposition alone."""
     r, nnz = t.coords.shape
     dev = t.coords.device
     ids = [torch.empty(nnz, dtype=torch.int32, device=dev) for _ in range(r)]
@@ -761,25 +764,43 @@ def bench_csf(qsd, t, plans, perms, cb, vbuf, ws, stream, reps: int = 5):
            for l in range(r + 1)]
     nodes = torch.empty(r + 1, dtype=torch.int32, device=dev)
     cws = torch.empty(qsd.csf_workspace_bytes(r, nnz), dtype=torch.uint8, device=dev)
+    fws = torch.empty(max(qsd.transpose_csf_workspace_bytes(p, nnz) for p in plans),
+                      dtype=torch.uint8, device=dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        ev0.record(stream)
+        for _ in range(reps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
     per = {}
     for p, sigma in zip(plans, perms):
         sel = qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, p, ws, stream)
         rows = cb[sel]
-        for _ in range(2):
-            qsd.csf_build(rows, sigma, ids, ptr, nodes, cws, stream)
-        ev0.record(stream)
-        for _ in range(reps):
-            qsd.csf_build(rows, sigma, ids, ptr, nodes, cws, stream)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1) / reps
+        ms_build = timed(lambda: qsd.csf_build(rows, sigma, ids, ptr, nodes, cws, stream))
         n = [int(x) for x in nodes.cpu()]
+        ms_t = timed(lambda: qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, p, ws, stream))
+        ms_f = timed(lambda: qsd.transpose_csf_from(t.coords, t.vals, cb, vbuf, nnz, p, ids, ptr,
+                                                    nodes, fws, stream))
+        if qsd.workspace_status(fws, stream) != 0:
+            raise SystemExit("device status set by the fused transposition")
         written = 4 * (sum(n[1:]) + sum(n) + 1 + r)  # ids and ptr entries
         per["".join(map(str, sigma))] = {
-            "ms": round(ms, 4), "gnnz_s": round(nnz / (ms / 1e3) / 1e9, 2),
-            "nodes": n, "gb_s": round((2 * 4 * r * nnz + written) / (ms / 1e3) / 1e9, 1)}
-    return {"what": "CSF levels of each transposed output (count, scan, write over the entries)",
+            "csf_build_ms": round(ms_build, 4), "transpose_ms": round(ms_t, 4),
+            "fused_ms": round(ms_f, 4), "fused_csf_ms": round(ms_f - ms_t, 4),
+            "separate_total_ms": round(ms_t + ms_build, 4),
+            "csf_build_gb_s": round((2 * 4 * r * nnz + written) / (ms_build / 1e3) / 1e9, 1),
+            "nodes": n}
+    tot_sep = sum(v["separate_total_ms"] for v in per.values())
+    tot_f = sum(v["fused_ms"] for v in per.values())
+    return {"what": "CSF levels of each transposed output: separate build (count and write "
+                    "sweeps over every row) vs fused into the transposition's last movement",
+            "sum_ms": {"separate": round(tot_sep, 3), "fused": round(tot_f, 3)},
             "per_order": per}
 
 

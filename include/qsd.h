@@ -349,6 +349,26 @@ qsd_status qsd_csf_build(const int32_t* coords, int64_t stride, int64_t nnz, int
                          const int* sigma, const qsd_csf* out, int32_t* nodes,
                          void* workspace, size_t workspace_bytes, void* stream);
 
+/* Transposition and the CSF levels of its result in one call: as
+ * qsd_transpose_from_ws followed by qsd_csf_build on the result (sigma =
+ * the plan's target order), but the comparisons of neighbouring output
+ * entries the levels are made of are done by the transposition's last
+ * movement, which has both entries in shared memory (the paper's closing
+ * section proposes fusing format conversion into the sort): it leaves one
+ * byte per entry, the first level at which the entry differs from the one
+ * before it (0 where that entry was written by another tile or bucket
+ * batch), and the CSF pass reads those bytes instead of every coordinate
+ * row, working out the unknown ones from the rows. Arguments as for
+ * qsd_transpose_from_ws and qsd_csf_build; `workspace` must hold
+ * qsd_transpose_csf_workspace_bytes(plan, nnz), 256-byte aligned. The
+ * tree is the same as qsd_csf_build gives. */
+qsd_status qsd_transpose_csf_workspace_bytes(qsd_plan_t plan, int64_t nnz, size_t* bytes);
+qsd_status qsd_transpose_csf_from_ws(const int32_t* in_coords, int64_t in_stride,
+                                     const void* in_vals, qsd_coords* out_coords,
+                                     qsd_values* out_vals, int64_t nnz, qsd_plan_t plan,
+                                     const qsd_csf* csf, int32_t* nodes, void* workspace,
+                                     size_t workspace_bytes, void* stream);
+
 /* ---- Batches ----
  * Many independent tensors transposed together. The paper transposes one
  * tensor at a time; a batch runs the same method (each tensor gets its own

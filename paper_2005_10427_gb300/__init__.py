@@ -395,6 +395,44 @@ def csf_levels(coords, sigma: Sequence[int], stream=None):
             [ptr[l][:n[l] + 1] for l in range(r + 1)])
 
 
+def transpose_csf_workspace_bytes(plan: "Plan", nnz: int) -> int:
+    need = ctypes.c_size_t()
+    _check(lib().qsd_transpose_csf_workspace_bytes(plan.handle, int(nnz), ctypes.byref(need)),
+           "qsd_transpose_csf_workspace_bytes")
+    return max(int(need.value), 256)
+
+
+def transpose_csf_from(in_coords, in_vals, cbuf: Sequence, vbuf: Optional[Sequence], nnz: int,
+                       plan: "Plan", ids, ptr, nodes, workspace, stream=None) -> int:
+    """qsd_transpose_csf_from_ws: out-of-place transposition into cbuf/vbuf
+    (returns the result's selector) and the CSF levels of the result into
+    preallocated int32 CUDA tensors ids[l] (capacity >= nnz), ptr[0] (2),
+    ptr[l] (nnz + 1) and nodes (r + 1), as csf_build gives them."""
+    r = plan.order
+    c = _capi.Coords()
+    c.buf[0] = cbuf[0].data_ptr()
+    c.buf[1] = cbuf[1].data_ptr()
+    c.stride = int(cbuf[0].stride(0))
+    v = _capi.Values()
+    if vbuf is not None:
+        v.buf[0] = vbuf[0].data_ptr()
+        v.buf[1] = vbuf[1].data_ptr()
+        v.elem_bytes = _val_bytes(vbuf[0])
+    out = _capi.Csf()
+    for l in range(r):
+        out.ids[l] = ids[l].data_ptr()
+    for l in range(r + 1):
+        out.ptr[l] = ptr[l].data_ptr()
+    st = lib().qsd_transpose_csf_from_ws(
+        ctypes.c_void_p(in_coords.data_ptr()), int(in_coords.stride(0)),
+        ctypes.c_void_p(in_vals.data_ptr()) if in_vals is not None else None,
+        ctypes.byref(c), ctypes.byref(v), int(nnz), plan.handle, ctypes.byref(out),
+        ctypes.c_void_p(nodes.data_ptr()), ctypes.c_void_p(workspace.data_ptr()),
+        int(workspace.numel()), _stream_handle(stream))
+    _check(st, "qsd_transpose_csf_from_ws")
+    return int(c.selector)
+
+
 def server_clock() -> float:
     """Seconds of the monotonic clock the server stamps times with."""
     return float(lib().qsd_server_clock())

@@ -122,6 +122,9 @@ SIGNATURES = [
                           ctypes.POINTER(ctypes.c_float)]),
     ("qsd_csf_workspace_bytes", I, [I, I64, ctypes.POINTER(ctypes.c_size_t)]),
     ("qsd_csf_build", I, [P, I64, I64, I, P, ctypes.POINTER(Csf), P, P, ctypes.c_size_t, P]),
+    ("qsd_transpose_csf_workspace_bytes", I, [P, I64, ctypes.POINTER(ctypes.c_size_t)]),
+    ("qsd_transpose_csf_from_ws", I, [P, I64, P, ctypes.POINTER(Coords), ctypes.POINTER(Values),
+                                      I64, P, ctypes.POINTER(Csf), P, P, ctypes.c_size_t, P]),
     ("qsd_batch_create", I, [ctypes.POINTER(BatchItem), I, I, ctypes.POINTER(BatchOptions),
                              ctypes.POINTER(P)]),
     ("qsd_batch_workspace_bytes", I, [P, ctypes.POINTER(ctypes.c_size_t)]),

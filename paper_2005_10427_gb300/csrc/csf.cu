@@ -33,7 +33,8 @@ struct CsfIn {
   const int32_t* col[kMaxOrder];  // the rows in sigma order: col[l] = row sigma_l
   int order;
   int nnz;
-  int vec;  // every row 16-byte aligned: 16-byte loads
+  int vec;       // every row 16-byte aligned: 16-byte loads
+  uint8_t* lev;  // L of every entry from the transposition (0 = unknown), or null
 };
 
 // The 16 values of row l at entries j0 .. j0 + 15 (j0 a multiple of 16), and
@@ -59,11 +60,60 @@ __device__ __forceinline__ void load_run(const CsfIn& in, int l, int j0, uint32_
   }
 }
 
+// L(j) of one entry from the rows (j > 0).
+__device__ __forceinline__ uint32_t level_at(const CsfIn& in, int j) {
+  for (int l = 0; l < in.order; ++l)
+    if (__ldg(in.col[l] + j) != __ldg(in.col[l] + j - 1)) return (uint32_t)l + 1;
+  return (uint32_t)in.order + 1;
+}
+
 // L(j) of the thread's 16 entries (4 bits each): the first level (1-based)
 // whose mode differs from the entry before (1 at entry 0, order + 1 for a
-// duplicate, order + 2 past the end). Reads the rows level by level.
-__device__ __forceinline__ void first_levels(const CsfIn& in, int j0, uint32_t (&L)[2]) {
+// duplicate, order + 2 past the end). Reads the rows level by level, or,
+// when the transposition left the levels (in.lev), reads those and works
+// out only the unknown ones from the rows (writing them back when
+// `fix` is set).
+__device__ __forceinline__ void first_levels(const CsfIn& in, int j0, uint32_t (&L)[2],
+                                             bool fix = false) {
   uint32_t lv[kCsfItems];
+  if (in.lev) {
+    uint8_t b[kCsfItems];
+    const bool full = j0 + kCsfItems <= in.nnz;
+    if (full) {
+      const uint4 x = *reinterpret_cast<const uint4*>(in.lev + j0);
+      const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+      for (int k = 0; k < kCsfItems; ++k) b[k] = (uint8_t)(w[k / 4] >> (8 * (k % 4)));
+    } else {
+#pragma unroll
+      for (int k = 0; k < kCsfItems; ++k) b[k] = j0 + k < in.nnz ? in.lev[j0 + k] : 0;
+    }
+    bool changed = false;
+#pragma unroll
+    for (int k = 0; k < kCsfItems; ++k) {
+      const int j = j0 + k;
+      if (j >= in.nnz) {
+        lv[k] = in.order + 2;
+      } else if (j == 0) {
+        lv[k] = 1;
+      } else if (b[k] == 0) {
+        lv[k] = level_at(in, j);
+        b[k] = (uint8_t)lv[k];
+        changed = true;
+      } else {
+        lv[k] = b[k];
+      }
+    }
+    if (fix && changed) {
+#pragma unroll
+      for (int k = 0; k < kCsfItems; ++k)
+        if (j0 + k < in.nnz) in.lev[j0 + k] = b[k];
+    }
+    L[0] = L[1] = 0;
+#pragma unroll
+    for (int k = 0; k < kCsfItems; ++k) L[k / 8] |= lv[k] << ((k % 8) * 4);
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < kCsfItems; ++k)
     lv[k] = j0 + k >= in.nnz ? in.order + 2 : (j0 + k == 0 ? 1 : in.order + 1);
@@ -92,7 +142,7 @@ k_csf_count(const __grid_constant__ CsfIn in, uint32_t* __restrict__ tile_count,
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, t = blockIdx.x;
   const int j0 = t * kCsfTile + threadIdx.x * kCsfItems;
   uint32_t L[2];
-  first_levels(in, j0, L);
+  first_levels(in, j0, L, true);
 #pragma unroll
   for (int l = 0; l < kMaxOrder; ++l) {
     if (l >= in.order) break;
@@ -171,20 +221,22 @@ k_csf_write(const __grid_constant__ CsfIn in, const uint32_t* __restrict__ tile_
     for (int k = 0; k < kCsfItems; ++k) c += level_of(L, k) <= (uint32_t)l + 1 ? 1u : 0u;
     uint32_t total;
     uint32_t p = tile_off[(size_t)l * ntiles + t] + block_exclusive_sum<kCsfWarps>(c, s_tmp, &total);
-    uint32_t v[kCsfItems], before;
-    load_run(in, l, j0, v, before);
+    if (c != 0) {  // else none of the thread's entries starts a node here: no ids to read
+      uint32_t v[kCsfItems], before;
+      load_run(in, l, j0, v, before);
 #pragma unroll
-    for (int k = 0; k < kCsfItems; ++k) {
-      const uint32_t lk = level_of(L, k);
-      if (lk <= (uint32_t)l + 1) {  // entry j0 + k starts a node on level l + 1
-        out.ids[l][p] = (int32_t)v[k];
-        if (lk <= (uint32_t)l) out.ptr[l][above[k]] = (int32_t)p;  // and its parent
-        if (l == in.order - 1) out.ptr[in.order][p] = j0 + k;
-        above[k] = p;
-        ++p;
+      for (int k = 0; k < kCsfItems; ++k) {
+        const uint32_t lk = level_of(L, k);
+        if (lk <= (uint32_t)l + 1) {  // entry j0 + k starts a node on level l + 1
+          out.ids[l][p] = (int32_t)v[k];
+          if (lk <= (uint32_t)l) out.ptr[l][above[k]] = (int32_t)p;  // and its parent
+          if (l == in.order - 1) out.ptr[in.order][p] = j0 + k;
+          above[k] = p;
+          ++p;
+        }
       }
     }
-    __syncthreads();  // s_tmp is reused by the next level's scan
+    __syncthreads();  // s_tmp is reused by the next level's scan (every thread)
   }
 }
 
@@ -192,11 +244,12 @@ k_csf_write(const __grid_constant__ CsfIn in, const uint32_t* __restrict__ tile_
 
 cudaError_t launch_csf(const int32_t* const* rows_in_sigma_order, int order, int nnz,
                        const CsfOut& out, int32_t* nodes, uint32_t* tile_count,
-                       cudaStream_t stream) {
+                       cudaStream_t stream, uint8_t* lev) {
   CsfIn in;
   in.order = order;
   in.nnz = nnz;
   in.vec = 1;
+  in.lev = lev;
   for (int l = 0; l < kMaxOrder; ++l) {
     in.col[l] = l < order ? rows_in_sigma_order[l] : nullptr;
     if (l < order && (reinterpret_cast<uintptr_t>(in.col[l]) & 15)) in.vec = 0;

@@ -385,7 +385,7 @@ template <int T, int NS, int VB, int RW, int WW>
 __global__ void __launch_bounds__(Roles<RW, WW>::kThreads, 1)
 k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls,
              const uint32_t* __restrict__ chunk_off, int* __restrict__ claim, unsigned* status,
-             PassBatch pb) {
+             PassBatch pb, const __grid_constant__ LevOut lv) {
   constexpr int kWsRankWarps = RW, kWsWriteWarps = WW;
   constexpr int kWsRankThreads = Roles<RW, WW>::kRank;
   constexpr int kWsWriteThreads = Roles<RW, WW>::kWrite;
@@ -632,6 +632,34 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
         dst_pos[k] = g;
         src_idx[k] = i;
       }
+      if (lv.lev) {
+        // the entry written just before position g is the one at sorted
+        // position p - 1 when that has the same digit (the same run of
+        // consecutive destinations); compare them level by level in sigma
+        // order
+#pragma unroll
+        for (int k = 0; k < WITEMS; ++k) {
+          const int p = k * kWsWriteThreads + t;
+          if (dst_pos[k] < 0) continue;
+          uint32_t L = 0;
+          const uint32_t x = S.invdig[j][p];
+          const uint32_t y = p > 0 ? S.invdig[j][p - 1] : 0xffffffffu;
+          if (p > 0 && (y >> 16) == (x >> 16)) {
+            const int a = src_idx[k], b = (int)(y & 0xffffu);
+            L = (uint32_t)lv.order + 1;
+            for (int l = 0; l < lv.order; ++l) {
+              const int m = lv.sigma[l];
+              const uint32_t* row = reinterpret_cast<const uint32_t*>(
+                  buf + (size_t)m * row_slot<T>(4) + ts.row[m].off);
+              if (row[a] != row[b]) {
+                L = (uint32_t)l + 1;
+                break;
+              }
+            }
+          }
+          lv.lev[dst_pos[k]] = (uint8_t)L;
+        }
+      }
       for (int r = 0; r < c.order; ++r) {
         const uint32_t* src =
             reinterpret_cast<const uint32_t*>(buf + (size_t)r * row_slot<T>(4) + ts.row[r].off);
@@ -663,7 +691,8 @@ size_t ws_smem(int order) {
 template <int T, int NS, int VB, int RW, int WW>
 cudaError_t launch_move_t(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
                           const uint32_t* chunk_off, int* claim, int max_chunks,
-                          unsigned* status, const PassBatch& pb, cudaStream_t stream) {
+                          unsigned* status, const PassBatch& pb, cudaStream_t stream,
+                          const LevOut& lv) {
   const size_t smem = ws_smem<T, NS, VB, RW>(c.order);
   cudaError_t e = cudaFuncSetAttribute(k_digit_move<T, NS, VB, RW, WW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -675,7 +704,7 @@ cudaError_t launch_move_t(const Cols& c, const LargeSegs& ls, const PassDesc& pd
   one.c = c;
   one.pd = pd;
   k_digit_move<T, NS, VB, RW, WW><<<grid, Roles<RW, WW>::kThreads, smem, stream>>>(
-      one, c.order, ls, chunk_off, claim, status, pb);
+      one, c.order, ls, chunk_off, claim, status, pb, lv);
   return cudaGetLastError();
 }
 
@@ -685,11 +714,12 @@ cudaError_t launch_move_t(const Cols& c, const LargeSegs& ls, const PassDesc& pd
 template <int VB>
 cudaError_t launch_move_vb(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
                            const uint32_t* chunk_off, int* claim, int max_chunks,
-                           unsigned* status, const PassBatch& pb, cudaStream_t stream) {
+                           unsigned* status, const PassBatch& pb, cudaStream_t stream,
+                           const LevOut& lv) {
   constexpr size_t kMax = 227 * 1024;
 #define QSD_MV(T_, NS_, RW_, WW_)                                                      \
   return launch_move_t<T_, NS_, VB, RW_, WW_>(c, ls, pd, chunk_off, claim, max_chunks, status, \
-                                              pb, stream)
+                                              pb, stream, lv)
   if (ls.tile == 4096) {
     if (ws_smem<4096, 3, VB, 16>(c.order) <= kMax) QSD_MV(4096, 3, 16, 15);
     QSD_MV(4096, 2, 16, 15);
@@ -771,11 +801,19 @@ cudaError_t debug_words_digit_pass(unsigned long long limit_ns, int stall) {
 
 cudaError_t launch_digit_move(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
                               const uint32_t* chunk_off, int* claim, int max_chunks,
-                              unsigned* status, const PassBatch& pb, cudaStream_t stream) {
+                              unsigned* status, const PassBatch& pb, cudaStream_t stream,
+                              const LevOut* lvp) {
+  LevOut lv;
+  if (lvp && !pb.t) {
+    lv = *lvp;
+  } else {
+    lv.lev = nullptr;
+    lv.order = 0;
+  }
   switch (c.vbytes) {
-    case 0: return launch_move_vb<0>(c, ls, pd, chunk_off, claim, max_chunks, status, pb, stream);
-    case 4: return launch_move_vb<4>(c, ls, pd, chunk_off, claim, max_chunks, status, pb, stream);
-    case 8: return launch_move_vb<8>(c, ls, pd, chunk_off, claim, max_chunks, status, pb, stream);
+    case 0: return launch_move_vb<0>(c, ls, pd, chunk_off, claim, max_chunks, status, pb, stream, lv);
+    case 4: return launch_move_vb<4>(c, ls, pd, chunk_off, claim, max_chunks, status, pb, stream, lv);
+    case 8: return launch_move_vb<8>(c, ls, pd, chunk_off, claim, max_chunks, status, pb, stream, lv);
   }
   return cudaErrorInvalidValue;
 }

@@ -126,7 +126,7 @@ struct Src {
 
 qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
                     int64_t nnz64, const qsd_plan_s* plan, void* ws, const Layout& L,
-                    cudaStream_t st) {
+                    cudaStream_t st, const LevOut* lv = nullptr) {
   const int nnz = (int)nnz64;
   uint8_t* base = static_cast<uint8_t*>(ws);
   unsigned* status = reinterpret_cast<unsigned*>(base + L.status);
@@ -203,9 +203,15 @@ qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
   ClassifyBatch cb1;
   std::memset(&cb1, 0, sizeof(cb1));
 
+  // the group whose movement leaves the entries in their final places: it
+  // also writes the CSF levels when asked (lv)
+  int last_moving = -1;
+  for (int gi = 0; gi < plan->ngroups; ++gi)
+    if (plan->groups[gi].npasses > 0) last_moving = gi;
   for (int gi = 0; gi < plan->ngroups && nnz > 0; ++gi) {
     const Group& g = plan->groups[gi];
     if (g.npasses == 0) continue;
+    const LevOut* glv = gi == last_moving ? lv : nullptr;
     PassList pl;
     pl.npasses = g.npasses;
     for (int p = 0; p < g.npasses; ++p) pl.pass[p] = g.pass[p];
@@ -285,7 +291,7 @@ qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
       const int F = internal ? cur.idx ^ 1 : 0;
       QSD_LAUNCH(tag("local_sort", gi, -1, nnz, 2 * R),
                  launch_local_sort(cols(cur, F), pl, nullptr, counters, 1, nnz, C, status, lb1,
-                                   st));
+                                   st, glv));
       cur = buf_src(F);
       continue;
     }
@@ -323,7 +329,7 @@ qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
       // small buckets: straight into F (in place when F is the input buffer)
       QSD_LAUNCH(tag("local_sort", gi, -1, -1, 2 * R, 1),
                  launch_local_sort(cols(cur, F), pl, seg_start, counters, 0, nnz, C, status,
-                                   lb1, st));
+                                   lb1, st, glv));
       ls.single = 0;
       ls.seg = large;
       ls.chunk_base = chunk_base;
@@ -352,7 +358,7 @@ qsd_status run_plan(qsd_coords* coords, qsd_values* vals, const Src* ext,
       QSD_LAUNCH(tag("digit_move", gi, p, large_entries, 2 * R),
                  launch_digit_move(cols(in, dst(p)), ls, g.pass[p], chunk_hist,
                                    counters + kCntClaim + 2 * p + 1, max_chunks, status, pb1,
-                                   st));
+                                   st, p == P - 1 ? glv : nullptr));
     }
     cur = buf_src(F);
   }
@@ -419,6 +425,84 @@ qsd_status qsd_transpose_from_ws(const int32_t* in_coords, int64_t in_stride,
   }
   return run_plan(out_coords, out_vals, nnz > 0 ? &ext : nullptr, nnz, plan, workspace, L,
                   (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// Transposition followed by the CSF levels of its result, the levels'
+// comparisons done by the transposition's last movement.
+namespace {
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+}  // namespace
+
+qsd_status qsd_transpose_csf_workspace_bytes(qsd_plan_t plan, int64_t nnz, size_t* bytes) {
+  if (!plan || !bytes || nnz < 0) return QSD_ERR_INVALID_ARGUMENT;
+  if (nnz > kMaxNnz) return QSD_ERR_UNSUPPORTED;
+  size_t t = 0, c = 0;
+  qsd_status s = qsd_workspace_bytes(plan, nnz, &t);
+  if (s == QSD_OK) s = qsd_csf_workspace_bytes(plan->order, nnz, &c);
+  if (s != QSD_OK) return s;
+  *bytes = align256(t) + align256((size_t)nnz + 16) + c;
+  return QSD_OK;
+}
+
+qsd_status qsd_transpose_csf_from_ws(const int32_t* in_coords, int64_t in_stride,
+                                     const void* in_vals, qsd_coords* out_coords,
+                                     qsd_values* out_vals, int64_t nnz, qsd_plan_t plan,
+                                     const qsd_csf* csf, int32_t* nodes, void* workspace,
+                                     size_t workspace_bytes, void* stream) {
+  if (!plan || !csf || !nodes) return QSD_ERR_INVALID_ARGUMENT;
+  const int r = plan->order;
+  for (int l = 0; l <= r; ++l) {
+    if (!csf->ptr[l]) return QSD_ERR_INVALID_ARGUMENT;
+    if (l < r && nnz > 0 && !csf->ids[l]) return QSD_ERR_INVALID_ARGUMENT;
+  }
+  size_t need = 0;
+  qsd_status s = qsd_transpose_csf_workspace_bytes(plan, nnz, &need);
+  if (s != QSD_OK) return s;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & (kAlign - 1)))
+    return QSD_ERR_INVALID_ARGUMENT;
+  if (workspace_bytes < need) return QSD_ERR_WORKSPACE_TOO_SMALL;
+  size_t tbytes = 0;
+  qsd_workspace_bytes(plan, nnz, &tbytes);
+  uint8_t* base = static_cast<uint8_t*>(workspace);
+  uint8_t* lev = base + align256(tbytes);
+  uint32_t* tile_count = reinterpret_cast<uint32_t*>(lev + align256((size_t)nnz + 16));
+  cudaStream_t st = (cudaStream_t)stream;
+  s = check_buffers(out_coords, out_vals, nnz, plan);
+  if (s != QSD_OK) return s;
+  const bool has_vals = out_vals && out_vals->elem_bytes != 0;
+  if (nnz > 0 && (!in_coords || in_stride < nnz)) return QSD_ERR_INVALID_ARGUMENT;
+  if (has_vals && nnz > 0 && !in_vals) return QSD_ERR_INVALID_ARGUMENT;
+  if (nnz > 0 && (in_coords == out_coords->buf[0] || in_coords == out_coords->buf[1]))
+    return QSD_ERR_INVALID_ARGUMENT;
+  const Layout L = layout_for(plan, nnz, has_vals ? out_vals->elem_bytes : 0);
+  Src ext;
+  ext.c = in_coords;
+  ext.v = has_vals ? in_vals : nullptr;
+  ext.stride = in_stride;
+  ext.idx = -1;
+  if (nnz == 0) {
+    out_coords->selector = 0;
+    if (has_vals) out_vals->selector = 0;
+  }
+  // every level byte the last movement does not write stays 0 (unknown)
+  if (nnz > 0) QSD_CUDA(cudaMemsetAsync(lev, 0, (size_t)nnz, st));
+  LevOut lv;
+  std::memset(&lv, 0, sizeof(lv));
+  lv.lev = lev;
+  lv.order = r;
+  for (int l = 0; l < r; ++l) lv.sigma[l] = plan->sigma[l];
+  s = run_plan(out_coords, out_vals, nnz > 0 ? &ext : nullptr, nnz, plan, workspace, L, st, &lv);
+  if (s != QSD_OK) return s;
+  const int32_t* res = out_coords->buf[out_coords->selector];
+  const int32_t* rows[QSD_MAX_ORDER];
+  for (int l = 0; l < r; ++l) rows[l] = nnz > 0 ? res + (int64_t)plan->sigma[l] * out_coords->stride
+                                                : nullptr;
+  CsfOut o;
+  for (int l = 0; l < kMaxOrder; ++l) o.ids[l] = l < r ? csf->ids[l] : nullptr;
+  for (int l = 0; l <= kMaxOrder; ++l) o.ptr[l] = l <= r ? csf->ptr[l] : nullptr;
+  QSD_CUDA(launch_csf(rows, r, (int)nnz, o, nodes, tile_count, st, lev));
+  return QSD_OK;
 }
 
 qsd_status qsd_transpose(qsd_coords* coords, qsd_values* vals, int64_t nnz,

@@ -159,10 +159,22 @@ cudaError_t launch_chunk_hist(const Cols& c, const LargeSegs& ls, const PassDesc
 cudaError_t launch_chunk_scan(const LargeSegs& ls, uint32_t* chunk_hist,
                               const uint32_t* group_sum, int max_groups, const PassBatch& pb,
                               cudaStream_t stream);
+// CSF levels from the last movement of a transposition: for every output
+// position g it writes lev[g] = the first level (1-based, in sigma order)
+// whose coordinate differs from the entry at g - 1 (order + 1: equal
+// coordinates), or 0 where the entry before g is not at hand (another tile
+// or batch); lev == nullptr: nothing written.
+struct LevOut {
+  uint8_t* lev;
+  int order;
+  int sigma[kMaxOrder];
+};
+
 // Moves every row of every chunk to its digit's slots, tile by tile.
 cudaError_t launch_digit_move(const Cols& c, const LargeSegs& ls, const PassDesc& pd,
                               const uint32_t* chunk_off, int* claim, int max_chunks,
-                              unsigned* status, const PassBatch& pb, cudaStream_t stream);
+                              unsigned* status, const PassBatch& pb, cudaStream_t stream,
+                              const LevOut* lv = nullptr);
 
 // The bucket capacity the shared-memory sort runs with: the largest power of
 // two in [1024, want] whose staged rows fit shared memory.
@@ -172,16 +184,20 @@ int local_sort_capacity(int want, int order, int vbytes);
 cudaError_t launch_local_sort(const Cols& c, const PassList& pl,
                               const int* seg_start, const int* counters,
                               int single, int nnz, int capacity,
-                              unsigned* status, const LsBatch& lb, cudaStream_t stream);
+                              unsigned* status, const LsBatch& lb, cudaStream_t stream,
+                              const LevOut* lv = nullptr);
 
 // CSF levels of a tensor sorted under sigma (rows given in sigma order).
 struct CsfOut {
   int32_t* ids[kMaxOrder];      // level l + 1 node ids
   int32_t* ptr[kMaxOrder + 1];  // level l: first child (l < order) / first entry (l == order)
 };
+// lev (nullable, nnz bytes, 16-byte aligned): the first differing level of
+// every entry as a transposition's last movement left it (0 = unknown);
+// the unknown ones are filled in from the rows first.
 cudaError_t launch_csf(const int32_t* const* rows_in_sigma_order, int order, int nnz,
                        const CsfOut& out, int32_t* nodes, uint32_t* tile_count,
-                       cudaStream_t stream);
+                       cudaStream_t stream, uint8_t* lev = nullptr);
 size_t csf_workspace_bytes(int order, int nnz);
 
 // Copies every coordinate row and the values from c.in to c.out (entries

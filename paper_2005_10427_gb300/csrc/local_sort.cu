@@ -103,7 +103,7 @@ template <int CAP, int VB>
 __global__ void __launch_bounds__(kLsThreads)
 k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict__ seg_start,
              const int* __restrict__ counters, int single, int nnz, LsBatch lb, int lay_order,
-             unsigned* status) {
+             unsigned* status, const __grid_constant__ LevOut lv) {
   constexpr int ITEMS = CAP / kLsThreads;
   constexpr size_t kRow4 = (size_t)CAP * 4 + 16;  // a staged coordinate row
   extern __shared__ __align__(16) uint8_t smem[];
@@ -385,6 +385,26 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
       T* dst = reinterpret_cast<T*>(c.vout) + A;
       for (int i = threadIdx.x; i < n; i += kLsThreads) dst[i] = src[S.perm[cur][i]];
     }
+    if (lv.lev) {
+      // first differing level against the entry written just before (the
+      // batch's first entry: unknown here)
+      for (int i = threadIdx.x; i < n; i += kLsThreads) {
+        uint32_t L = 0;
+        if (i > 0) {
+          const int a = S.perm[cur][i], b = S.perm[cur][i - 1];
+          L = (uint32_t)lv.order + 1;
+          for (int l = 0; l < lv.order; ++l) {
+            const int m = lv.sigma[l];
+            const uint32_t* row = reinterpret_cast<const uint32_t*>(row_smem(m) + S.row_off[m]);
+            if (row[a] != row[b]) {
+              L = (uint32_t)l + 1;
+              break;
+            }
+          }
+        }
+        lv.lev[A + i] = (uint8_t)L;
+      }
+    }
     __syncthreads();  // the stage is free for the next batch
     s = e;
   }
@@ -393,7 +413,7 @@ k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict
 template <int CAP, int VB>
 cudaError_t launch_ls(const Cols& c, const PassList& pl, const int* seg_start,
                       const int* counters, int single, int nnz, const LsBatch& lb,
-                      unsigned* status, cudaStream_t stream) {
+                      unsigned* status, cudaStream_t stream, const LevOut& lv) {
   // shared state, then the staged rows: c.order coordinate rows (the largest
   // order of a batch) and the value row
   const size_t smem = ls_smem<CAP>(c.order, VB);
@@ -404,18 +424,19 @@ cudaError_t launch_ls(const Cols& c, const PassList& pl, const int* seg_start,
   const int grid = single ? 1 : (int)(((int64_t)nnz + (int64_t)CAP * kLsSpan - 1) / ((int64_t)CAP * kLsSpan));
   if (grid < 1) return cudaSuccess;
   k_local_sort<CAP, VB><<<grid, kLsThreads, smem, stream>>>(c, pl, seg_start, counters,
-                                                            single, nnz, lb, c.order, status);
+                                                            single, nnz, lb, c.order, status,
+                                                            lv);
   return cudaGetLastError();
 }
 
 template <int CAP>
 cudaError_t launch_ls_cap(const Cols& c, const PassList& pl, const int* seg_start,
                           const int* counters, int single, int nnz, const LsBatch& lb,
-                          unsigned* status, cudaStream_t stream) {
+                          unsigned* status, cudaStream_t stream, const LevOut& lv) {
   switch (c.vbytes) {
-    case 0: return launch_ls<CAP, 0>(c, pl, seg_start, counters, single, nnz, lb, status, stream);
-    case 4: return launch_ls<CAP, 4>(c, pl, seg_start, counters, single, nnz, lb, status, stream);
-    case 8: return launch_ls<CAP, 8>(c, pl, seg_start, counters, single, nnz, lb, status, stream);
+    case 0: return launch_ls<CAP, 0>(c, pl, seg_start, counters, single, nnz, lb, status, stream, lv);
+    case 4: return launch_ls<CAP, 4>(c, pl, seg_start, counters, single, nnz, lb, status, stream, lv);
+    case 8: return launch_ls<CAP, 8>(c, pl, seg_start, counters, single, nnz, lb, status, stream, lv);
   }
   return cudaErrorInvalidValue;
 }
@@ -444,12 +465,20 @@ int local_sort_capacity(int want, int order, int vbytes) {
 
 cudaError_t launch_local_sort(const Cols& c, const PassList& pl, const int* seg_start,
                               const int* counters, int single, int nnz, int capacity,
-                              unsigned* status, const LsBatch& lb, cudaStream_t stream) {
+                              unsigned* status, const LsBatch& lb, cudaStream_t stream,
+                              const LevOut* lvp) {
+  LevOut lv;
+  if (lvp && lb.n == 0) {
+    lv = *lvp;
+  } else {
+    lv.lev = nullptr;
+    lv.order = 0;
+  }
   switch (capacity) {
-    case 1024: return launch_ls_cap<1024>(c, pl, seg_start, counters, single, nnz, lb, status, stream);
-    case 2048: return launch_ls_cap<2048>(c, pl, seg_start, counters, single, nnz, lb, status, stream);
-    case 4096: return launch_ls_cap<4096>(c, pl, seg_start, counters, single, nnz, lb, status, stream);
-    case 8192: return launch_ls_cap<8192>(c, pl, seg_start, counters, single, nnz, lb, status, stream);
+    case 1024: return launch_ls_cap<1024>(c, pl, seg_start, counters, single, nnz, lb, status, stream, lv);
+    case 2048: return launch_ls_cap<2048>(c, pl, seg_start, counters, single, nnz, lb, status, stream, lv);
+    case 4096: return launch_ls_cap<4096>(c, pl, seg_start, counters, single, nnz, lb, status, stream, lv);
+    case 8192: return launch_ls_cap<8192>(c, pl, seg_start, counters, single, nnz, lb, status, stream, lv);
   }
   return cudaErrorInvalidValue;
 }
