@@ -120,6 +120,12 @@ typedef struct {
                             result, fewer bytes per pass, one random read of
                             every entry. Needs 8 (key <= 32 bits) or 12 bytes
                             per entry more workspace */
+  int first_digit_bits;  /* 0 < b < the digit width: the least significant
+                            digit of every group takes b bits and the rest
+                            of the key is split evenly, where that needs no
+                            more passes than the even split (fewer runs per
+                            tile where the key's low bits are near uniform);
+                            0 = even split. 0 <= b <= 8 */
 } qsd_plan_options;
 
 /* Description of a plan (qsd_plan_get_info). */

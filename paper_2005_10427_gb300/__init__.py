@@ -62,7 +62,7 @@ class Plan:
                  validate: bool = False, digit_bits: int = 0,
                  local_capacity: int = 0, no_skip: bool = False, tile: int = 0,
                  chunk_tiles: int = 0, global_groups: bool = False, top_k: int = 0,
-                 key_index: bool = False):
+                 key_index: bool = False, first_digit_bits: int = 0):
         L = lib()
         r = len(dims)
         self.dims = [int(d) for d in dims]
@@ -72,12 +72,13 @@ class Plan:
             [int(x) for x in input_mode_order]
         opts = _capi.PlanOptions(int(bool(validate)), int(digit_bits), int(local_capacity),
                                  int(bool(no_skip)), int(tile), int(chunk_tiles),
-                                 int(bool(global_groups)), int(top_k), int(bool(key_index)))
+                                 int(bool(global_groups)), int(top_k), int(bool(key_index)),
+                                 int(first_digit_bits))
         self.options = dict(validate=bool(validate), digit_bits=int(digit_bits),
                             local_capacity=int(local_capacity), no_skip=bool(no_skip),
                             tile=int(tile), chunk_tiles=int(chunk_tiles),
                             global_groups=bool(global_groups), top_k=int(top_k),
-                            key_index=bool(key_index))
+                            key_index=bool(key_index), first_digit_bits=int(first_digit_bits))
         handle = ctypes.c_void_p()
         dims_arr = (ctypes.c_int64 * max(r, 1))(*self.dims)
         st = L.qsd_plan_ex(r, dims_arr, _i32(self.input_mode_order) if r else None,
@@ -343,7 +344,7 @@ def tune_plan(plan: "Plan", in_coords, in_vals, reps: int = 3, stream=None):
                  local_capacity=opts["local_capacity"], no_skip=bool(opts["no_skip"]),
                  tile=opts["tile"], chunk_tiles=opts["chunk_tiles"],
                  global_groups=bool(opts["global_groups"]), top_k=opts["top_k"],
-                 key_index=bool(opts["key_index"]))
+                 key_index=bool(opts["key_index"]), first_digit_bits=opts["first_digit_bits"])
     return tuned, float(ms.value), opts
 
 

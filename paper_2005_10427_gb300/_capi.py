@@ -30,7 +30,7 @@ class PlanOptions(ctypes.Structure):
                 ("local_capacity", ctypes.c_int), ("no_skip", ctypes.c_int),
                 ("tile", ctypes.c_int), ("chunk_tiles", ctypes.c_int),
                 ("global_groups", ctypes.c_int), ("top_k", ctypes.c_int),
-                ("key_index", ctypes.c_int)]
+                ("key_index", ctypes.c_int), ("first_digit_bits", ctypes.c_int)]
 
 
 _A = ctypes.c_int * MAX_ORDER

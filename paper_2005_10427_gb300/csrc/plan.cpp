@@ -34,9 +34,13 @@ bool is_perm(int order, const int* p) {
 }
 
 // Splits the packed key of group g into LSD-first digit passes of at most
-// `digit_bits` bits, as even as possible. False when that takes more passes
-// than a group holds.
-bool schedule_digits(const int64_t* dims, qsd::Group& g, int digit_bits) {
+// `digit_bits` bits, as even as possible; with first_bits (0 < first_bits <
+// digit_bits) the least significant digit takes first_bits bits and the
+// rest is split evenly, when that needs no more passes than the even split
+// (a narrower first digit spreads each tile over fewer runs where the key's
+// low bits are near uniform). False when the passes exceed what a group
+// holds.
+bool schedule_digits(const int64_t* dims, qsd::Group& g, int digit_bits, int first_bits) {
   int base[QSD_MAX_ORDER], width[QSD_MAX_ORDER];
   int acc = 0;
   for (int i = g.nkeys - 1; i >= 0; --i) {  // last key mode = lowest bits
@@ -51,10 +55,21 @@ bool schedule_digits(const int64_t* dims, qsd::Group& g, int digit_bits) {
   }
   int np = (acc + digit_bits - 1) / digit_bits;
   if (np > qsd::kMaxPasses) return false;
+  // the first digit's width, then the rest split evenly over np - 1 passes
+  int first = 0;
+  if (first_bits > 0 && first_bits < digit_bits && np >= 2 &&
+      1 + (acc - first_bits + digit_bits - 1) / digit_bits <= np)
+    first = first_bits;
   g.npasses = np;
   int lo = 0;
   for (int p = 0; p < np; ++p) {
-    int bits = acc / np + (p < acc % np ? 1 : 0);
+    int bits;
+    if (first) {
+      const int rest = acc - first, nr = np - 1;
+      bits = p == 0 ? first : rest / nr + (p - 1 < rest % nr ? 1 : 0);
+    } else {
+      bits = acc / np + (p < acc % np ? 1 : 0);
+    }
     int hi = lo + bits;
     qsd::PassDesc& d = g.pass[p];
     d.nfields = 0;
@@ -137,6 +152,8 @@ qsd_status qsd_plan_ex(int order, const int64_t* dims,
     return QSD_ERR_INVALID_ARGUMENT;
   if (o.chunk_tiles < 0 || o.chunk_tiles > 256) return QSD_ERR_INVALID_ARGUMENT;
   if (o.top_k < 0 || o.top_k > QSD_MAX_ORDER) return QSD_ERR_INVALID_ARGUMENT;
+  if (o.first_digit_bits < 0 || o.first_digit_bits > qsd::kRadixBits)
+    return QSD_ERR_INVALID_ARGUMENT;
 
   qsd_plan_s* p = new (std::nothrow) qsd_plan_s;
   if (!p) return QSD_ERR_OUT_OF_MEMORY;
@@ -242,7 +259,7 @@ qsd_status qsd_plan_ex(int order, const int64_t* dims,
     }
   }
   for (int i = 0; i < p->ngroups; ++i)
-    if (!schedule_digits(p->dims, p->groups[i], p->digit_bits)) {
+    if (!schedule_digits(p->dims, p->groups[i], p->digit_bits, o.first_digit_bits)) {
       delete p;
       return QSD_ERR_UNSUPPORTED;  // a key too wide for the digit width
     }

@@ -7,8 +7,9 @@
 // the buckets of the first K target modes), whether groups with a prefix
 // sort bucket by bucket or as one global sort by (prefix, key), the radix
 // digit width (how many passes), the tile and chunk sizes, the bucket
-// capacity of the shared-memory sort, and whether groups without a prefix
-// sort (key, index) pairs and gather the entries once at the end.
+// capacity of the shared-memory sort, whether groups without a prefix sort
+// (key, index) pairs and gather the entries once at the end, and the width
+// of the least significant digit.
 // Each candidate is timed with CUDA events over real out-of-place
 // transpositions of the caller's data; a coordinate search keeps the fastest.
 #include <cuda_runtime.h>
@@ -33,8 +34,9 @@ bool has_prefix_group(const qsd_plan_s* p) {
 
 // The values each option takes in the search (0 = the library's choice);
 // top_k takes 0 .. order - 2.
-constexpr int kDims = 7;
+constexpr int kDims = 8;
 const int kKeyIndex[] = {0, 1};
+const int kFirstDigit[] = {0, 6, 5, 7};
 const int kStructure[] = {0, 1};
 const int kDigits[] = {8, 7, 6, 5};
 const int kTiles[] = {0, 4096, 3584, 2048};
@@ -51,6 +53,7 @@ void for_each_candidate_value(int dim, int order, F f) {
     case 4: for (int v : kCaps) f(v); break;
     case 5: for (int v : kChunks) f(v); break;
     case 6: for (int v : kKeyIndex) f(v); break;
+    case 7: for (int v : kFirstDigit) f(v); break;
   }
 }
 
@@ -62,7 +65,8 @@ int& field(qsd_plan_options& o, int dim) {
     case 3: return o.tile;
     case 4: return o.local_capacity;
     case 5: return o.chunk_tiles;
-    default: return o.key_index;
+    case 6: return o.key_index;
+    default: return o.first_digit_bits;
   }
 }
 

@@ -302,3 +302,16 @@ def test_key_index_form_of_groups(L):
     d3 = [1 << 20] * 3
     p2 = qsd.Plan(d3, (2, 1, 0), key_index=True)  # 40-bit key: two words
     assert p2.workspace_bytes(n) - qsd.Plan(d3, (2, 1, 0)).workspace_bytes(n) >= 2 * 12 * n
+
+
+def test_first_digit_bits_never_adds_passes(L):
+    dims = [4800000, 1700000, 1800000, 1100]
+    for sigma in itertools.permutations(range(4)):
+        if sigma == (0, 1, 2, 3):
+            continue
+        plain = [g["passes"] for g in qsd.Plan(dims, sigma).info()["groups"]]
+        for b in range(1, 9):
+            got = [g["passes"] for g in qsd.Plan(dims, sigma, first_digit_bits=b).info()["groups"]]
+            assert got == plain, (sigma, b)
+    with pytest.raises(qsd.QsdError):
+        qsd.Plan(dims, (3, 2, 1, 0), first_digit_bits=9)

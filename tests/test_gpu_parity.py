@@ -386,3 +386,15 @@ def test_key_index_multi_group_plans(qsd):
     coords, vals = tensor(dims, 300_000, seed=91, val_kind="f64_uniform", zipf=1.3)
     for sigma in [(1, 0, 3, 2), (2, 0, 3, 1), (3, 0, 2, 1), (1, 2, 3, 0), (3, 2, 1, 0)]:
         check(qsd, coords, vals, dims, sigma, key_index=True)
+
+
+@pytest.mark.parametrize("first", [1, 3, 5, 6, 7])
+def test_first_digit_widths(qsd, first):
+    # a narrower least significant digit, the rest of the key split evenly
+    dims = [300, 2000, 3000, 1100]
+    coords, vals = tensor(dims, 120_000, seed=50 + first, val_kind="f64_uniform", zipf=1.2,
+                          dup=0.05)
+    for sigma in [(1, 2, 3, 0), (3, 0, 1, 2), (0, 3, 2, 1), (2, 1, 0, 3), (1, 3, 0, 2)]:
+        check(qsd, coords, vals, dims, sigma, first_digit_bits=first, local_capacity=1024)
+        check(qsd, coords, vals, dims, sigma, first_digit_bits=first, key_index=True,
+              local_capacity=1024)
