@@ -96,9 +96,41 @@ __device__ __forceinline__ void copy_words(D* dst, const D* src, int t, int step
 }
 
 // ---------------------------------------------------------------------------
-// Chunk histograms: 16-byte loads of the digit's rows (four in flight per
-// thread), each vector of four consecutive entries counted into the warp's
-// histogram with one shared atomic per run of equal digits.
+// Counts a lane's four consecutive digits into its warp's histogram h (valid
+// lanes only; every lane of the warp calls it together). Lanes whose four
+// digits are equal -- most of them where one bin takes most entries -- are
+// combined across the warp: one match finds the lanes with the same digit
+// and one of them adds 4 per lane, so a hot bin takes one shared atomic per
+// warp instead of one per lane. Other lanes add one atomic per run of equal
+// digits.
+__device__ __forceinline__ void count4(uint32_t* h, const uint32_t (&e)[4], bool valid,
+                                       int lane) {
+  const bool same = valid && e[0] == e[1] && e[1] == e[2] && e[2] == e[3];
+  const uint32_t m_same = __ballot_sync(0xffffffffu, same);
+  if (same) {
+    const uint32_t peers = __match_any_sync(m_same, e[0]);
+    if (lane == __ffs(peers) - 1) atomicAdd(&h[e[0]], 4u * (uint32_t)__popc(peers));
+  } else if (valid) {
+    uint32_t run_d = e[0], run_n = 1;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+      if (e[k] == run_d) {
+        ++run_n;
+      } else {
+        atomicAdd(&h[run_d], run_n);
+        run_d = e[k];
+        run_n = 1;
+      }
+    }
+    atomicAdd(&h[run_d], run_n);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Chunk histograms: 16-byte loads of the digit's rows (eight or four in
+// flight per thread), each vector of four consecutive entries counted into
+// the warp's histogram (count4). The vector loops run with warp-uniform
+// bounds so that every lane takes part in count4's warp operations.
 __global__ void __launch_bounds__(kHistThreads)
 k_chunk_hist(const __grid_constant__ PassTensor one, LargeSegs ls,
              uint32_t* __restrict__ chunk_hist, uint32_t* __restrict__ group_sum,
@@ -106,7 +138,7 @@ k_chunk_hist(const __grid_constant__ PassTensor one, LargeSegs ls,
   __shared__ uint32_t s_hist[kHistWarps][kRadix];
   __shared__ int s_chunk;
   __shared__ PassTensor s_it;  // the chunk's tensor: buffers and digit
-  const int w = threadIdx.x >> 5;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nc = pb.t ? pb.counters[kCntPassChunks + pb.pass] : n_chunks(ls);
   const Cols& c = s_it.c;
   const PassDesc& pd = s_it.pd;
@@ -165,7 +197,8 @@ k_chunk_hist(const __grid_constant__ PassTensor one, LargeSegs ls,
       const DigitField fd = pd.f[0];
       const uint4* col =
           reinterpret_cast<const uint4*>(c.in + (int64_t)fd.mode * c.in_stride + vbeg);
-      for (int q0 = threadIdx.x; q0 < nvec; q0 += kHistThreads * 8) {
+      // the warp's first lane decides the trip count (lanes differ by < 32)
+      for (int q0 = threadIdx.x; q0 - lane < nvec; q0 += kHistThreads * 8) {
         uint4 v[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -174,25 +207,13 @@ k_chunk_hist(const __grid_constant__ PassTensor one, LargeSegs ls,
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          if (q0 + u * kHistThreads >= nvec) break;
           const uint32_t e[4] = {field_bits(v[u].x, fd), field_bits(v[u].y, fd),
                                  field_bits(v[u].z, fd), field_bits(v[u].w, fd)};
-          uint32_t run_d = e[0], run_n = 1;
-#pragma unroll
-          for (int k = 1; k < 4; ++k) {
-            if (e[k] == run_d) {
-              ++run_n;
-            } else {
-              atomicAdd(&s_hist[w][run_d], run_n);
-              run_d = e[k];
-              run_n = 1;
-            }
-          }
-          atomicAdd(&s_hist[w][run_d], run_n);
+          count4(s_hist[w], e, q0 + u * kHistThreads < nvec, lane);
         }
       }
     }
-    for (int q0 = threadIdx.x; q0 < (pd.nfields == 1 ? 0 : nvec); q0 += kHistThreads * 4) {
+    for (int q0 = threadIdx.x; q0 - lane < (pd.nfields == 1 ? 0 : nvec); q0 += kHistThreads * 4) {
       uint4 dv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) dv[u] = make_uint4(0, 0, 0, 0);
@@ -216,20 +237,8 @@ k_chunk_hist(const __grid_constant__ PassTensor one, LargeSegs ls,
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (q0 + u * kHistThreads >= nvec) break;
         const uint32_t e[4] = {dv[u].x, dv[u].y, dv[u].z, dv[u].w};
-        uint32_t run_d = e[0], run_n = 1;
-#pragma unroll
-        for (int k = 1; k < 4; ++k) {
-          if (e[k] == run_d) {
-            ++run_n;
-          } else {
-            atomicAdd(&s_hist[w][run_d], run_n);
-            run_d = e[k];
-            run_n = 1;
-          }
-        }
-        atomicAdd(&s_hist[w][run_d], run_n);
+        count4(s_hist[w], e, q0 + u * kHistThreads < nvec, lane);
       }
     }
     __syncthreads();
