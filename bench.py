@@ -208,7 +208,8 @@ def run_reference(args, rank, world):
     import oracle
     wl = WORKLOADS[args.workload]
     nnz = args.nnz or wl["nnz"]
-    sample = min(nnz, args.ref_sample)
+    ref_sample = args.ref_sample or (2_000_000 if len(wl["perms"]) <= 5 else 1_000_000)
+    sample = min(nnz, ref_sample)
     w = synth.scaled(wl, sample) if sample != wl["nnz"] else wl
     t = synth.make(w)
     coords, vals = t.coords.numpy(), t.vals.numpy()
@@ -251,7 +252,9 @@ def main():
     ap.add_argument("--perms", default="", help="comma-separated subset, e.g. 021,102")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--ref-sample", type=int, default=2_000_000)
+    ap.add_argument("--ref-sample", type=int, default=0,
+                    help="entries the reference arm sorts per order and step (0: 2M for up to 5 "
+                         "orders, 1M above, so that a step stays a few seconds)")
     ap.add_argument("--check", action="store_true", help="sampled parity check vs the oracle")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 256-tensor batched-vs-single-calls measurement")
