@@ -1,17 +1,25 @@
 """Benchmark: COO transposition throughput on one GB300 (and N replicas).
 
-Workload (default): a 3-order tensor of 12000 x 9000 x 28000 with 76M
-distinct coordinates drawn Zipf(1.1) per mode, float32 values N(0,1), sorted
-in (0,1,2) order and resident in HBM. One step transposes it into each of the
-5 non-identity target orders (out of place, the input stays intact), so a
-step moves 5 x 76M entries. Throughput = entries transposed per second
-(Gnnz/s), device-timed with CUDA events; the inputs (2.4 GB) are larger than
-the 129 MB L2, so no flush is needed between steps.
+Workload (default, the line of record): a 4-order tensor of 4.8M x 1.7M x
+1.8M x 1100 with 140M distinct coordinates (Zipf 1.3 on modes 0-2, uniform
+mode 3), float64 values N(0,1), sorted in (0,1,2,3) order and resident in
+HBM. One step transposes it into each of the 23 non-identity target orders
+(out of place, the input stays intact; each order's call captured once into
+a CUDA graph and replayed), so a step moves 23 x 140M entries. Throughput =
+entries transposed per second (Gnnz/s), device-timed with CUDA events; the
+input (3.4 GB) is larger than the 129 MB L2, so no flush is needed between
+steps.
 
 Also reported: the live roofline of the dominant kernel (algorithmic bytes /
-CUDA-event duration against the measured HBM copy bandwidth), the end-to-end
-rate through qsd_transpose_host with host buffers, SM clocks sampled during
-the timed region, and the CPU oracle's rate on a bounded sample.
+CUDA-event duration against the measured HBM copy bandwidth) and the whole
+step's fraction of the minimum-traffic roofline; per target order the time
+and fraction beside the no-skip radix sort, the key-index form and
+Top-K-sadilla; the same table for the 76M-entry order-3 workload; the
+1M-entry single-call latency; CSF levels; the batched workload against
+single calls; the serving workload (Poisson arrivals, saturated, and the
+same requests as single calls); the end-to-end rate through the host-buffer
+calls; SM clocks sampled during the timed region; and the CPU oracle's and
+the paper's CPU method's rates on bounded samples.
 
 `--impl reference` times the CPU oracle (std::stable_sort on the host cores)
 on bounded samples of the same workload instead.
@@ -266,6 +274,9 @@ def main():
                     help="skip Top-K-sadilla in the per-order table")
     ap.add_argument("--no-orders", action="store_true",
                     help="skip the per-order table (times, roofline fractions, no-skip ablation)")
+    ap.add_argument("--graphs", type=int, default=1,
+                    help="1: every order's call captured once into a CUDA graph (qsd_exec_*) "
+                         "and the timed step replays the graphs")
     ap.add_argument("--tune", type=int, default=0,
                     help="1: tune every order's plan with qsd_plan_tune (measured choice among "
                          "equivalent executions) before the timed region")
@@ -317,8 +328,18 @@ def main():
     cb = [torch.empty((r, nnz), dtype=torch.int32, device=dev) for _ in range(2)]
     vbuf = [torch.empty(nnz, dtype=t.vals.dtype, device=dev) for _ in range(2)]
     stream = torch.cuda.current_stream()
+    execs = [qsd.Exec(t.coords, t.vals, cb, vbuf, nnz, p, ws) for p in plans] \
+        if args.graphs else None
 
     def step():
+        if execs is not None:
+            for ex in execs:
+                ex.launch(stream)
+            return
+        for p in plans:
+            qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, p, ws, stream)
+
+    def step_plain():  # per-kernel timing (the launch profiler cannot see into graphs)
         for p in plans:
             qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, p, ws, stream)
 
@@ -355,7 +376,7 @@ def main():
     qsd.profile_reset()
     qsd.profile_enable(True)
     for _ in range(args.steps):
-        step()
+        step_plain()
     torch.cuda.synchronize()
     recs = qsd.profile_read()
     qsd.profile_enable(False)
@@ -485,6 +506,8 @@ def main():
                            "out_of_place": True, "parallelism": f"replicas{world}",
                            "plans": "tuned (qsd_plan_tune per order, before the timed region)"
                                     if args.tune else "default options",
+                           "calls": "CUDA graphs (qsd_exec_*), one per order" if args.graphs
+                                    else "qsd_transpose_from_ws",
                            "l2": "inputs (%.2f GB) larger than L2; no flush" % (nnz * R / 1e9)},
                 "roofline": roofline,
                 "min_traffic_frac": roofline["whole_step_frac"],
@@ -521,8 +544,9 @@ def bench_batched(qsd, dev, stream, steps: int, warmup: int, tune: bool = True):
     """The batched workload: 256 tensors (orders 3-5, log-uniform sizes in
     [1e3, 4e6] and dims in [100, 1e6], Zipf 1.1, float32 values, identity
     input order, a random non-identity target each) transposed by one graph
-    launch per step, against the same tensors as back-to-back single calls;
-    every output of both is compared bit for bit."""
+    launch per step, against the same tensors as back-to-back single calls
+    (plain, and each captured once into a CUDA graph); every output of all
+    three is compared bit for bit."""
     descs = synth.batch_workload()
     tens = [synth.gen_coo(d["dims"], d["nnz"], d["dists"], d["val_kind"], d["seed"], dev)
             for d in descs]
@@ -580,6 +604,32 @@ def bench_batched(qsd, dev, stream, steps: int, warmup: int, tune: bool = True):
     same = all(torch.equal(outs[i][0][batch.result(i)], souts[i][0][sels[i]]) and
                torch.equal(outs[i][1][batch.result(i)].view(torch.int32),
                            souts[i][1][sels[i]].view(torch.int32)) for i in range(len(tens)))
+
+    # the same single calls, each captured once into a CUDA graph (qsd_exec_*)
+    wss = [torch.empty(max(p.workspace_bytes(t.nnz), 256), dtype=torch.uint8, device=dev)
+           for p, t in zip(plans, tens)]
+    execs = [qsd.Exec(t.coords, t.vals, o[0], o[1], t.nnz, p, w)
+             for p, t, o, w in zip(plans, tens, souts, wss)]
+    gsels = [0] * len(tens)
+
+    def singles_graphs():
+        for i, ex in enumerate(execs):
+            gsels[i] = ex.launch(stream)
+
+    for _ in range(warmup):
+        singles_graphs()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        singles_graphs()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_g = ev0.elapsed_time(ev1) / steps
+    same = same and all(
+        torch.equal(outs[i][0][batch.result(i)], souts[i][0][gsels[i]]) and
+        torch.equal(outs[i][1][batch.result(i)].view(torch.int32),
+                    souts[i][1][gsels[i]].view(torch.int32)) for i in range(len(tens)))
+    del execs, wss
     peak, _ = measured_peaks()
     return {"workload": "batch256_r3-5_nnz1e3-4e6_zipf1.1_f32", "tensors": len(tens),
             "nnz_total": total, "steps": steps, "warmup": warmup,
@@ -588,7 +638,12 @@ def bench_batched(qsd, dev, stream, steps: int, warmup: int, tune: bool = True):
                         "min_traffic_frac": round(2 * R_bytes / (ms_b / 1e3) / 1e9 / peak, 4)},
             "single_calls": {"value": round(total / (ms_s / 1e3) / 1e9, 3), "unit": "Gnnz/s",
                              "ms_per_step": round(ms_s, 4)},
-            "speedup": round(ms_s / ms_b, 3), "identical_outputs": bool(same),
+            "single_calls_graphs": {"value": round(total / (ms_g / 1e3) / 1e9, 3),
+                                    "unit": "Gnnz/s", "ms_per_step": round(ms_g, 4),
+                                    "what": "each call captured once into a CUDA graph"},
+            "speedup": round(ms_s / ms_b, 3),
+            "speedup_vs_graph_calls": round(ms_g / ms_b, 3),
+            "identical_outputs": bool(same),
             "tuned_options": tuned, "tune_seconds": None if tune_s is None else round(tune_s, 2)}
 
 
@@ -922,28 +977,37 @@ def bench_other_workload(qsd, wl, dev, stream, reps: int = 5):
 def bench_latency(qsd, wl, dev, stream, calls: int = 50):
     """Latency of one single out-of-place call on a small tensor (1M entries
     fit the L2 cache, so this measures launch and latency, not bandwidth):
-    CUDA events around every call, min and median."""
+    CUDA events around every call, min and median; plain calls, the key-index
+    form, and the call captured into a CUDA graph (qsd_exec_*)."""
     t = synth.make(wl, device=dev)
     r, nnz = t.coords.shape
     out = {"workload": wl["name"]}
-    for sigma, kw in [(s, kw) for s in wl["perms"] for kw in ({}, {"key_index": True})]:
+    variants = [(s, kw, g) for s in wl["perms"]
+                for kw, g in (({}, False), ({"key_index": True}, False), ({}, True))]
+    for sigma, kw, graph in variants:
         p = qsd.Plan(wl["dims"], sigma, **kw)
         ws = torch.empty(p.workspace_bytes(nnz), dtype=torch.uint8, device=dev)
         cb = [torch.empty((r, nnz), dtype=torch.int32, device=dev) for _ in range(2)]
         vbuf = [torch.empty(nnz, dtype=t.vals.dtype, device=dev) for _ in range(2)]
+        if graph:  # the call captured once into a CUDA graph (qsd_exec_*)
+            ex = qsd.Exec(t.coords, t.vals, cb, vbuf, nnz, p, ws)
+            call = lambda: ex.launch(stream)  # noqa: E731
+        else:
+            call = lambda: qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, p, ws,  # noqa: E731
+                                              stream)
         for _ in range(5):
-            qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, p, ws, stream)
+            call()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(calls)]
         for a, b in evs:
             a.record(stream)
-            qsd.transpose_from(t.coords, t.vals, cb, vbuf, nnz, p, ws, stream)
+            call()
             b.record(stream)
         torch.cuda.synchronize()
         if qsd.workspace_status(ws, stream) != 0:
             raise SystemExit("device status set in the latency run")
         us = sorted(a.elapsed_time(b) * 1e3 for a, b in evs)
-        out["".join(map(str, sigma)) + ("_key_index" if kw else "")] = {
+        out["".join(map(str, sigma)) + ("_key_index" if kw else "") + ("_graph" if graph else "")] = {
             "min_us": round(us[0], 1), "median_us": round(us[len(us) // 2], 1),
             "gnnz_s_at_median": round(nnz / (us[len(us) // 2] / 1e6) / 1e9, 2),
             "groups": _groups(p)}

@@ -286,6 +286,33 @@ qsd_status qsd_workspace_status(const void* workspace, void* stream,
  * status word, which every transpose on that device ORs its errors into. */
 qsd_status qsd_get_async_status(void* stream, qsd_status* out);
 
+/* ---- Graph-captured calls ----
+ * One out-of-place transposition (the arguments of qsd_transpose_from_ws)
+ * captured once into a CUDA graph and replayed by a single graph launch per
+ * call: for repeated transpositions of resident tensors, especially small
+ * ones, whose time otherwise goes to launching a dozen or so kernels and
+ * memsets one by one. The pointers, nnz and plan are bound at creation and
+ * must stay valid (and unmodified in meaning) until qsd_exec_destroy; the
+ * input must be re-filled in place if it changes. Each launch computes the
+ * whole transposition anew, writes the same output buffer every time (its
+ * selector is returned), and uses the workspace like qsd_transpose_from_ws
+ * (its status word reports device errors; launches that may overlap on the
+ * device must not share a workspace). (No counterpart in the paper.)
+ *
+ * qsd_exec_create captures without running anything on the device; it
+ * returns the argument errors of qsd_transpose_from_ws, and
+ * QSD_ERR_UNSUPPORTED while the launch profiler is on.
+ * qsd_exec_launch launches on `stream` and stores the result's selectors
+ * (coordinates and values; either pointer may be NULL).
+ * qsd_exec_destroy releases the graph. NULL is ignored. */
+typedef struct qsd_exec_s* qsd_exec_t;
+qsd_status qsd_exec_create(const int32_t* in_coords, int64_t in_stride, const void* in_vals,
+                           const qsd_coords* out_coords, const qsd_values* out_vals,
+                           int64_t nnz, qsd_plan_t plan, void* workspace,
+                           size_t workspace_bytes, qsd_exec_t* out);
+qsd_status qsd_exec_launch(qsd_exec_t exec, void* stream, int* selector, int* vals_selector);
+void qsd_exec_destroy(qsd_exec_t exec);
+
 /* ---- Bounded waits: test-only controls ----
  * Every wait of a kernel on another part of itself (a staging buffer that a
  * bulk copy fills, a hand-off between its warps) gives up after a limit,

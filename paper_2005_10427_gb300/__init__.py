@@ -211,6 +211,48 @@ def transpose_noalloc(cbuf: Sequence, vbuf: Optional[Sequence], selector: int, n
     return int(c.selector)
 
 
+class Exec:
+    """One out-of-place transposition captured into a CUDA graph
+    (qsd_exec_*): launch() replays it. The tensors given here stay bound to
+    it (keep them alive and in place); launch() returns the selector of the
+    result buffer."""
+
+    def __init__(self, in_coords, in_vals, cbuf: Sequence, vbuf: Optional[Sequence], nnz: int,
+                 plan: Plan, workspace):
+        L = lib()
+        c = _capi.Coords()
+        c.buf[0] = cbuf[0].data_ptr()
+        c.buf[1] = cbuf[1].data_ptr()
+        c.stride = int(cbuf[0].stride(0))
+        v = _capi.Values()
+        if vbuf is not None:
+            v.buf[0] = vbuf[0].data_ptr()
+            v.buf[1] = vbuf[1].data_ptr()
+            v.elem_bytes = _val_bytes(vbuf[0])
+        h = ctypes.c_void_p()
+        st = L.qsd_exec_create(
+            ctypes.c_void_p(in_coords.data_ptr()), int(in_coords.stride(0)),
+            ctypes.c_void_p(in_vals.data_ptr()) if in_vals is not None else None,
+            ctypes.byref(c), ctypes.byref(v), int(nnz), plan.handle,
+            ctypes.c_void_p(workspace.data_ptr()), int(workspace.numel()), ctypes.byref(h))
+        _check(st, "qsd_exec_create")
+        self._h = h
+        self._lib = L
+        self._keep = (in_coords, in_vals, cbuf, vbuf, plan, workspace)
+
+    def launch(self, stream=None) -> int:
+        sel = ctypes.c_int()
+        _check(self._lib.qsd_exec_launch(self._h, _stream_handle(stream), ctypes.byref(sel),
+                                         None), "qsd_exec_launch")
+        return int(sel.value)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.qsd_exec_destroy(h)
+            self._h = None
+
+
 _OPTION_KEYS = ("digit_bits", "local_capacity", "tile", "chunk_tiles", "no_graph",
                 "use_tuned")
 

@@ -114,6 +114,10 @@ SIGNATURES = [
                                      ctypes.POINTER(Values), P, ctypes.c_size_t, P]),
     ("qsd_workspace_status", I, [P, P, ctypes.POINTER(I)]),
     ("qsd_get_async_status", I, [P, ctypes.POINTER(I)]),
+    ("qsd_exec_create", I, [P, I64, P, ctypes.POINTER(Coords), ctypes.POINTER(Values), I64, P,
+                            P, ctypes.c_size_t, ctypes.POINTER(P)]),
+    ("qsd_exec_launch", I, [P, P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+    ("qsd_exec_destroy", None, [P]),
     ("qsd_debug_set_spin_limit_ns", I, [ctypes.c_uint64]),
     ("qsd_debug_set_stall", I, [I]),
     ("qsd_plan_tune_workspace_bytes", I, [P, I64, ctypes.POINTER(ctypes.c_size_t)]),

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <new>
 
 #include "kernels.cuh"
 
@@ -503,6 +504,98 @@ qsd_status qsd_transpose_csf_from_ws(const int32_t* in_coords, int64_t in_stride
   for (int l = 0; l <= kMaxOrder; ++l) o.ptr[l] = l <= r ? csf->ptr[l] : nullptr;
   QSD_CUDA(launch_csf(rows, r, (int)nnz, o, nodes, tile_count, st, lev));
   return QSD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// A transposition captured once into a CUDA graph (qsd_exec_*): its launches
+// replayed by one graph launch, which removes the host's per-launch cost and
+// most of the gaps between dependent kernels.
+struct qsd_exec_s {
+  cudaGraphExec_t exec = nullptr;
+  int selector = 0;
+  int vselector = 0;
+};
+
+qsd_status qsd_exec_create(const int32_t* in_coords, int64_t in_stride, const void* in_vals,
+                           const qsd_coords* out_coords, const qsd_values* out_vals,
+                           int64_t nnz, qsd_plan_t plan, void* workspace,
+                           size_t workspace_bytes, qsd_exec_t* out) {
+  if (!out || !out_coords) return QSD_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  qsd_coords oc = *out_coords;
+  qsd_values ov;
+  std::memset(&ov, 0, sizeof(ov));
+  if (out_vals) ov = *out_vals;
+  qsd_status s = check_buffers(&oc, out_vals ? &ov : nullptr, nnz, plan);
+  if (s != QSD_OK) return s;
+  const bool has_vals = out_vals && out_vals->elem_bytes != 0;
+  if (nnz > 0 && (!in_coords || in_stride < nnz)) return QSD_ERR_INVALID_ARGUMENT;
+  if (has_vals && nnz > 0 && !in_vals) return QSD_ERR_INVALID_ARGUMENT;
+  if (nnz > 0 && (in_coords == oc.buf[0] || in_coords == oc.buf[1]))
+    return QSD_ERR_INVALID_ARGUMENT;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & (kAlign - 1)))
+    return QSD_ERR_INVALID_ARGUMENT;
+  const Layout L = layout_for(plan, nnz, has_vals ? ov.elem_bytes : 0);
+  if (workspace_bytes < L.total) return QSD_ERR_WORKSPACE_TOO_SMALL;
+  // the launch profiler records events of its own: nothing to capture it into
+  if (prof_enabled()) return QSD_ERR_UNSUPPORTED;
+  Src ext;
+  ext.c = in_coords;
+  ext.v = has_vals ? in_vals : nullptr;
+  ext.stride = in_stride;
+  ext.idx = -1;
+  if (nnz == 0) {
+    oc.selector = 0;
+    ov.selector = 0;
+  }
+  qsd_exec_s* e = new (std::nothrow) qsd_exec_s;
+  if (!e) return QSD_ERR_OUT_OF_MEMORY;
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete e;
+    return QSD_ERR_CUDA;
+  }
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamDestroy(cs);
+    delete e;
+    return QSD_ERR_CUDA;
+  }
+  s = run_plan(&oc, has_vals ? &ov : nullptr, nnz > 0 ? &ext : nullptr, nnz, plan, workspace, L,
+               cs);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (s == QSD_OK && (ce != cudaSuccess || !g)) s = QSD_ERR_CUDA;
+  if (s == QSD_OK && cudaGraphInstantiate(&e->exec, g, 0) != cudaSuccess) {
+    e->exec = nullptr;
+    s = QSD_ERR_CUDA;
+  }
+  if (g) cudaGraphDestroy(g);
+  if (s != QSD_OK) {
+    cudaGetLastError();
+    delete e;
+    return s;
+  }
+  e->selector = oc.selector;
+  e->vselector = ov.selector;
+  *out = e;
+  return QSD_OK;
+}
+
+qsd_status qsd_exec_launch(qsd_exec_t e, void* stream, int* selector, int* vals_selector) {
+  if (!e || !e->exec) return QSD_ERR_INVALID_ARGUMENT;
+  QSD_CUDA(cudaGraphLaunch(e->exec, (cudaStream_t)stream));
+  if (selector) *selector = e->selector;
+  if (vals_selector) *vals_selector = e->vselector;
+  return QSD_OK;
+}
+
+void qsd_exec_destroy(qsd_exec_t e) {
+  if (!e) return;
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  delete e;
 }
 
 qsd_status qsd_transpose(qsd_coords* coords, qsd_values* vals, int64_t nnz,

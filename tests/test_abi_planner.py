@@ -315,3 +315,22 @@ def test_first_digit_bits_never_adds_passes(L):
             assert got == plain, (sigma, b)
     with pytest.raises(qsd.QsdError):
         qsd.Plan(dims, (3, 2, 1, 0), first_digit_bits=9)
+
+
+def test_exec_create_checks_arguments_before_device_work(L):
+    p = qsd.Plan([4, 4], [1, 0])
+    c = _capi.Coords()
+    c.buf[0], c.buf[1] = 1 << 36, 2 << 36
+    c.stride = 10
+    h = ctypes.c_void_p()
+    src = ctypes.c_void_p(3 << 36)
+    assert L.qsd_exec_create(src, 10, None, ctypes.byref(c), None, 10, p.handle,
+                             ctypes.c_void_p(4 << 36), 1 << 20, None) == 1       # no out
+    assert L.qsd_exec_create(src, 10, None, ctypes.byref(c), None, 10, p.handle,
+                             ctypes.c_void_p((4 << 36) + 8), 1 << 20, ctypes.byref(h)) == 1  # alignment
+    assert L.qsd_exec_create(src, 9, None, ctypes.byref(c), None, 10, p.handle,
+                             ctypes.c_void_p(4 << 36), 1 << 20, ctypes.byref(h)) == 1   # stride < nnz
+    assert L.qsd_exec_create(src, 10, None, ctypes.byref(c), None, 10, p.handle,
+                             ctypes.c_void_p(4 << 36), 16, ctypes.byref(h)) == 9        # workspace
+    assert L.qsd_exec_launch(None, None, None, None) == 1
+    L.qsd_exec_destroy(None)

@@ -196,3 +196,35 @@ def test_empty_tensor_and_f32_values(qsd):
     torch.cuda.synchronize()
     assert torch.equal(oc, sc) and torch.equal(ov.view(torch.int32), sv.view(torch.int32))
     srv.close()
+
+
+@pytest.mark.parametrize("val_kind,vb", [("f64_normal", 8), ("f32_normal", 4)])
+def test_served_mix_each_result_matches_oracle(qsd, val_kind, vb):
+    # every result of a mix served on two streams in continuous batches (arrivals
+    # while earlier steps run, orders 3 and 4, every target order) against the
+    # oracle's transposition of the same tensor
+    tens = pool(5, seed=11 + vb, nnz_hi=250_000, val_kind=val_kind)
+    srv = qsd.Server(1 << 30, val_bytes=vb, max_batch=6, streams=2)
+    ids = [srv.add_tensor(t.coords, t.vals, t.dims) for t in tens]
+    host = [(t.coords.cpu().numpy(), t.vals.cpu().numpy()) for t in tens]
+    rng = np.random.default_rng(31 + vb)
+    reqs = {}
+    for k in range(36):
+        i = int(rng.integers(0, len(tens)))
+        sigma = tuple(int(x) for x in rng.permutation(tens[i].order))
+        reqs[srv.submit(ids[i], sigma)] = (i, sigma)
+        if k % 6 == 5:
+            time.sleep(0.002)
+    got = collect(srv, len(reqs))
+    bits = np.uint64 if vb == 8 else np.uint32
+    for rid, (i, sigma) in reqs.items():
+        assert got[rid]["status"] == 0
+        oc = torch.empty_like(tens[i].coords)
+        ov = torch.empty_like(tens[i].vals)
+        srv.copy_result(rid, oc, ov)
+        torch.cuda.synchronize()
+        rc, rv = oracle.transpose(host[i][0], host[i][1], sigma)
+        assert np.array_equal(oc.cpu().numpy(), rc), (rid, sigma)
+        assert np.array_equal(ov.cpu().numpy().view(bits), rv.view(bits)), (rid, sigma)
+        srv.release(rid)
+    srv.close()
