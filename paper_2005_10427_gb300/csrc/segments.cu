@@ -123,6 +123,74 @@ k_seg_count(PrefixCols pc1, SegBatch sb, int nnz, uint32_t* __restrict__ bits,
   }
 }
 
+// k_seg_count for one tensor whose prefix rows are 16-byte aligned: each lane
+// reads four consecutive entries per row with one 16-byte load, so a warp
+// covers its 512 entries in four rounds of 128. The flags of a round are the
+// lanes' 4-bit groups; lanes 8q .. 8q+7 together give word q of the round
+// (entries 32q .. 32q+31), the same words k_seg_count stores.
+__global__ void __launch_bounds__(kSegThreads)
+k_seg_count_vec(PrefixCols pc, int nnz, uint32_t* __restrict__ bits,
+                uint32_t* __restrict__ tile_count) {
+  __shared__ uint32_t s_warp[kSegWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int t = blockIdx.x;
+  const int j0 = t * kSegTile;
+  const int j1 = min(j0 + kSegTile, nnz);
+  const int np = pc.n;
+  const int base = j0 + w * kSegItems * 32;
+  const int wbase = t * (kSegTile / 32) + w * kSegItems;
+  int32_t prev[kMaxOrder];
+  // the entry before this warp's first one (lane 0's predecessor in round 0)
+#pragma unroll
+  for (int m = 0; m < kMaxOrder; ++m)
+    prev[m] = (m < np && base > 0 && base - 1 < j1) ? __ldg(pc.col[m] + base - 1) : 0;
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int r = 0; r < kSegItems / 4; ++r) {
+    const int jv = base + r * 128 + 4 * lane;  // the lane's first entry
+    uint32_t nib = 0;
+#pragma unroll
+    for (int m = 0; m < kMaxOrder; ++m) {
+      if (m >= np) break;
+      int4 v;
+      if (jv + 4 <= j1) {
+        v = __ldg(reinterpret_cast<const int4*>(pc.col[m] + jv));
+      } else {
+        v.x = jv < j1 ? __ldg(pc.col[m] + jv) : 0;
+        v.y = jv + 1 < j1 ? __ldg(pc.col[m] + jv + 1) : 0;
+        v.z = jv + 2 < j1 ? __ldg(pc.col[m] + jv + 2) : 0;
+        v.w = jv + 3 < j1 ? __ldg(pc.col[m] + jv + 3) : 0;
+      }
+      // entry jv - 1: lane-1's last, or for lane 0 the previous round's lane 31
+      int32_t p = __shfl_up_sync(0xffffffffu, v.w, 1);
+      const int32_t last = __shfl_sync(0xffffffffu, v.w, 31);
+      if (lane == 0) p = prev[m];
+      prev[m] = last;
+      nib |= (v.x != p ? 1u : 0u) | (v.y != v.x ? 2u : 0u) | (v.z != v.y ? 4u : 0u) |
+             (v.w != v.z ? 8u : 0u);
+    }
+    if (jv == 0) nib |= 1u;  // the tensor's first entry starts a bucket
+    const int nvalid = j1 - jv;
+    nib &= nvalid >= 4 ? 15u : (nvalid > 0 ? (1u << nvalid) - 1u : 0u);
+    uint32_t word = nib << (4 * (lane & 7));
+    word |= __shfl_xor_sync(0xffffffffu, word, 1);
+    word |= __shfl_xor_sync(0xffffffffu, word, 2);
+    word |= __shfl_xor_sync(0xffffffffu, word, 4);
+    const int q = lane >> 3;
+    if ((lane & 7) == 0 && base + r * 128 + 32 * q < j1) bits[wbase + r * 4 + q] = word;
+    cnt += __popc(nib);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) s_warp[w] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int k = 0; k < kSegWarps; ++k) tot += s_warp[k];
+    tile_count[t] = tot;
+  }
+}
+
 __global__ void __launch_bounds__(1024)
 k_seg_scan(uint32_t* __restrict__ tile_count, int ntiles, int nnz, int* __restrict__ seg_start,
            int* __restrict__ counters) {
@@ -276,7 +344,12 @@ cudaError_t launch_seg_discover(const int32_t* const* prefix_cols, int nprefix,
   // seg_lb holds the tile counts (ntiles words) followed by the flag bits
   uint32_t* tile_count = seg_lb;
   uint32_t* bits = seg_lb + ntiles + 1;
-  k_seg_count<<<ntiles, kSegThreads, 0, stream>>>(pc, sb, nnz, bits, tile_count);
+  bool aligned = true;  // every prefix row 16-byte aligned: 16-byte loads
+  for (int m = 0; m < nprefix; ++m) aligned &= (reinterpret_cast<uintptr_t>(pc.col[m]) & 15) == 0;
+  if (aligned)
+    k_seg_count_vec<<<ntiles, kSegThreads, 0, stream>>>(pc, nnz, bits, tile_count);
+  else
+    k_seg_count<<<ntiles, kSegThreads, 0, stream>>>(pc, sb, nnz, bits, tile_count);
   k_seg_scan<<<1, 1024, 0, stream>>>(tile_count, ntiles, nnz, seg_start, counters);
   k_seg_write<<<ntiles, kSegThreads, 0, stream>>>(sb, nnz, bits, tile_count, seg_start);
   return cudaGetLastError();
