@@ -254,10 +254,70 @@ k_chunk_hist(const __grid_constant__ PassTensor one, LargeSegs ls,
 }
 
 // ---------------------------------------------------------------------------
+// Group offsets of a pass over one whole tensor (ls.single): one block turns
+// the chunk groups' digit counts into each group's first output slot per
+// digit, in place: group_sum[g][d] <- (entries of smaller digits) + (entries
+// of digit d in groups before g). Thread (part, d) takes digit d over a
+// quarter of the groups; eight counts in flight per thread.
+constexpr int kPrefixParts = 4;
+__global__ void __launch_bounds__(kRadix * kPrefixParts)
+k_group_prefix(LargeSegs ls, uint32_t* __restrict__ group_sum) {
+  __shared__ uint32_t s_part[kPrefixParts][kRadix];
+  __shared__ uint32_t s_below[kRadix];
+  __shared__ uint32_t s_warp[kRadix / 32];
+  const int d = threadIdx.x % kRadix, part = threadIdx.x / kRadix;
+  const int ng = n_groups(ls);
+  const int per = (ng + kPrefixParts - 1) / kPrefixParts;
+  const int g0 = min(part * per, ng), g1 = min(g0 + per, ng);
+  uint32_t sum = 0;
+  for (int g = g0; g < g1; g += 8) {
+    uint32_t v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = g + k < g1 ? group_sum[(size_t)(g + k) * kRadix + d] : 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += v[k];
+  }
+  s_part[part][d] = sum;
+  __syncthreads();
+  if (part == 0) {  // the digit totals' exclusive scan (warps 0-7)
+    uint32_t tot = 0;
+#pragma unroll
+    for (int k = 0; k < kPrefixParts; ++k) tot += s_part[k][d];
+    const int lane = d & 31, w = d >> 5;
+    uint32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[w] = incl;
+    s_below[d] = incl - tot;  // within the warp for now
+  }
+  __syncthreads();
+  uint32_t run = s_below[d];
+  for (int k = 0; k < (d >> 5); ++k) run += s_warp[k];
+  for (int k = 0; k < part; ++k) run += s_part[k][d];
+  for (int g = g0; g < g1; g += 8) {
+    uint32_t v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = g + k < g1 ? group_sum[(size_t)(g + k) * kRadix + d] : 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (g + k < g1) {
+        group_sum[(size_t)(g + k) * kRadix + d] = run;
+        run += v[k];
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Chunk offsets. One block (kRadix threads, one per digit) per chunk group.
+// Over one whole tensor of more than 16 groups the group's first slots come
+// from k_group_prefix; otherwise each block adds up its bucket's groups.
 __global__ void __launch_bounds__(kRadix)
 k_chunk_scan(LargeSegs ls, uint32_t* __restrict__ chunk_hist,
-             const uint32_t* __restrict__ group_sum, PassBatch pb) {
+             const uint32_t* __restrict__ group_sum, PassBatch pb, int prefixed) {
+  // prefixed: group_sum holds k_group_prefix's first slots (one whole tensor)
   __shared__ uint32_t s_tmp[kRadix / 32 + 1];
   const int d = threadIdx.x;
   const int ng_all = pb.t ? pb.counters[kCntPassGroups + pb.pass] : n_groups(ls);
@@ -282,16 +342,21 @@ k_chunk_scan(LargeSegs ls, uint32_t* __restrict__ chunk_hist,
       lo = se.x;
     }
     (void)s;
-    // bucket total and the sum over the bucket's earlier groups, per digit
-    uint32_t total = 0, prior = 0;
-    for (int g = gb; g < gb + ng; ++g) {
-      const uint32_t v = group_sum[(size_t)g * kRadix + d];
-      total += v;
-      if (g < G) prior += v;
+    uint32_t off;
+    if (prefixed) {
+      off = group_sum[(size_t)G * kRadix + d];  // k_group_prefix's first slot
+    } else {
+      // bucket total and the sum over the bucket's earlier groups, per digit
+      uint32_t total = 0, prior = 0;
+      for (int g = gb; g < gb + ng; ++g) {
+        const uint32_t v = group_sum[(size_t)g * kRadix + d];
+        total += v;
+        if (g < G) prior += v;
+      }
+      uint32_t tot_all;
+      const uint32_t below = block_exclusive_sum<kRadix / 32>(total, s_tmp, &tot_all);
+      off = (uint32_t)lo + below + prior;
     }
-    uint32_t tot_all;
-    const uint32_t below = block_exclusive_sum<kRadix / 32>(total, s_tmp, &tot_all);
-    uint32_t off = (uint32_t)lo + below + prior;
     const int c0 = cb + (G - gb) * kGroupChunks;
     const int c1 = min(c0 + kGroupChunks, cb + nc);
     for (int c = c0; c < c1; c += 8) {
@@ -795,12 +860,15 @@ cudaError_t launch_chunk_hist(const Cols& c, const LargeSegs& ls, const PassDesc
 }
 
 cudaError_t launch_chunk_scan(const LargeSegs& ls, uint32_t* chunk_hist,
-                              const uint32_t* group_sum, int max_groups, const PassBatch& pb,
+                              uint32_t* group_sum, int max_groups, const PassBatch& pb,
                               cudaStream_t stream) {
   int grid = sm_count() * 8;
   if (grid > max_groups) grid = max_groups;
   if (grid < 1) grid = 1;
-  k_chunk_scan<<<grid, kRadix, 0, stream>>>(ls, chunk_hist, group_sum, pb);
+  // with few groups each block's own sum over them is cheaper than a launch more
+  const int prefixed = ls.single && !pb.t && max_groups > 16;
+  if (prefixed) k_group_prefix<<<1, kRadix * kPrefixParts, 0, stream>>>(ls, group_sum);
+  k_chunk_scan<<<grid, kRadix, 0, stream>>>(ls, chunk_hist, group_sum, pb, prefixed);
   return cudaGetLastError();
 }
 

@@ -156,8 +156,10 @@ cudaError_t launch_chunk_hist(const Cols& c, const LargeSegs& ls, const PassDesc
                               int max_chunks, const PassBatch& pb, cudaStream_t stream);
 // Per chunk group: turns chunk_hist into each chunk's first output slot per
 // digit (bucket start + digits below + the same digit in earlier chunks).
+// Over one whole tensor (ls.single, no batch) of more than 16 chunk groups,
+// group_sum is first turned, in place, into each group's first slot per digit.
 cudaError_t launch_chunk_scan(const LargeSegs& ls, uint32_t* chunk_hist,
-                              const uint32_t* group_sum, int max_groups, const PassBatch& pb,
+                              uint32_t* group_sum, int max_groups, const PassBatch& pb,
                               cudaStream_t stream);
 // CSF levels from the last movement of a transposition: for every output
 // position g it writes lev[g] = the first level (1-based, in sigma order)
