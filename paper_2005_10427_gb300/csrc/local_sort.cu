@@ -28,8 +28,13 @@ namespace qsd {
 
 namespace {
 
-constexpr int kLsThreads = 512;
-constexpr int kLsWarps = kLsThreads / 32;
+// Threads of a block: 512 for capacities of 4096 entries and more, 256
+// below, where the smaller per-warp counter space lets three blocks share an
+// SM (the sort is barrier-bound, and more blocks hide each other's waits).
+template <int CAP>
+constexpr int ls_threads() {
+  return CAP >= 4096 ? 512 : 256;
+}
 constexpr int kTiny = 64;  // largest bucket of the rank-by-counting path
 constexpr int kLsSpan = 4;  // windows of CAP entries per block
 
@@ -44,10 +49,11 @@ struct LsVal<8> {
 
 template <int CAP>
 struct LsShared {
-  uint32_t warp_hist[kLsWarps * kRadix];
+  static constexpr int kWarps = ls_threads<CAP>() / 32;
+  uint32_t warp_hist[kWarps * kRadix];
   uint32_t bin_start[kRadix];
   uint32_t bin_count[kRadix];
-  uint32_t tmp[kLsWarps + 1];
+  uint32_t tmp[kWarps + 1];
   uint16_t perm[2][CAP];
   uint16_t segid[CAP];
   int first, last, batch_end;
@@ -100,10 +106,12 @@ __device__ __forceinline__ void copy_passes(PassDesc* dst, const PassDesc* src, 
 }
 
 template <int CAP, int VB>
-__global__ void __launch_bounds__(kLsThreads)
+__global__ void __launch_bounds__(ls_threads<CAP>())
 k_local_sort(Cols c1, const __grid_constant__ PassList pl, const int* __restrict__ seg_start,
              const int* __restrict__ counters, int single, int nnz, LsBatch lb, int lay_order,
              unsigned* status, const __grid_constant__ LevOut lv) {
+  constexpr int kLsThreads = ls_threads<CAP>();
+  constexpr int kLsWarps = kLsThreads / 32;
   constexpr int ITEMS = CAP / kLsThreads;
   constexpr size_t kRow4 = (size_t)CAP * 4 + 16;  // a staged coordinate row
   extern __shared__ __align__(16) uint8_t smem[];
@@ -423,7 +431,7 @@ cudaError_t launch_ls(const Cols& c, const PassList& pl, const int* seg_start,
   if (e != cudaSuccess) return e;
   const int grid = single ? 1 : (int)(((int64_t)nnz + (int64_t)CAP * kLsSpan - 1) / ((int64_t)CAP * kLsSpan));
   if (grid < 1) return cudaSuccess;
-  k_local_sort<CAP, VB><<<grid, kLsThreads, smem, stream>>>(c, pl, seg_start, counters,
+  k_local_sort<CAP, VB><<<grid, ls_threads<CAP>(), smem, stream>>>(c, pl, seg_start, counters,
                                                             single, nnz, lb, c.order, status,
                                                             lv);
   return cudaGetLastError();
@@ -449,8 +457,9 @@ cudaError_t debug_words_local_sort(unsigned long long limit_ns, int stall) {
 
 // The bucket capacity the sort runs with: the largest power of two in
 // [1024, want] whose staged rows leave room for two blocks per SM (the
-// loads of one block overlap the ranking of the other), else the largest
-// that fits shared memory at all.
+// loads of one block overlap the ranking of the other; below 4096 entries
+// the smaller blocks leave room for three), else the largest that fits
+// shared memory at all.
 int local_sort_capacity(int want, int order, int vbytes) {
   constexpr size_t kMax = 227 * 1024, kTwo = 113 * 1024;
   const size_t sz[4] = {ls_smem<8192>(order, vbytes), ls_smem<4096>(order, vbytes),
