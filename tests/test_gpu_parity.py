@@ -398,3 +398,30 @@ def test_first_digit_widths(qsd, first):
         check(qsd, coords, vals, dims, sigma, first_digit_bits=first, local_capacity=1024)
         check(qsd, coords, vals, dims, sigma, first_digit_bits=first, key_index=True,
               local_capacity=1024)
+
+
+@pytest.mark.parametrize("opts", [{}, {"key_index": True}, {"global_groups": True}])
+def test_unaligned_rows_and_odd_strides(qsd, opts):
+    # rows that are not 16-byte aligned (odd row strides, buffers starting one
+    # element into an allocation) take the scalar paths of the vectorised
+    # kernels (boundary count, histograms, pack, gather, copies)
+    dims = [300, 2000, 500, 40]
+    coords, vals = tensor(dims, 90_001, seed=71, val_kind="f64_uniform", zipf=1.1)
+    r, n = coords.shape
+    stride = n + 3
+    for sigma in [(0, 2, 1, 3), (3, 2, 1, 0), (1, 0, 3, 2), (0, 1, 2, 3)]:
+        plan = qsd.Plan(dims, sigma, local_capacity=1024, **opts)
+        big_in = torch.zeros(r * stride + 1, dtype=torch.int32, device="cuda")
+        cin = big_in[1:].view(r, stride)[:, :n]
+        cin.copy_(torch.from_numpy(coords).cuda())
+        vin = torch.zeros(n + 1, dtype=torch.float64, device="cuda")[1:]
+        vin.copy_(torch.from_numpy(vals).cuda())
+        outs = [torch.zeros(r * stride + 1, dtype=torch.int32, device="cuda")[1:].view(r, stride)
+                for _ in range(2)]
+        vouts = [torch.zeros(n + 1, dtype=torch.float64, device="cuda")[1:] for _ in range(2)]
+        ws = torch.empty(plan.workspace_bytes(n), dtype=torch.uint8, device="cuda")
+        sel = qsd.transpose_from(cin, vin, outs, vouts, n, plan, ws)
+        assert qsd.workspace_status(ws) == 0
+        rc, rv = oracle.transpose(coords, vals, sigma)
+        assert np.array_equal(outs[sel][:, :n].cpu().numpy(), rc), (sigma, opts)
+        assert np.array_equal(vouts[sel].cpu().numpy().view(np.uint64), rv.view(np.uint64))
