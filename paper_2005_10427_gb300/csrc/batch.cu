@@ -649,11 +649,11 @@ qsd_status qsd_batch_tune(qsd_batch_t b, void* workspace, size_t workspace_bytes
   // coordinate search: one option at a time, keeping the fastest
   const int tiles[] = {4096, 3584, 2048, 1024};
   const int bits[] = {8, 7, 6};
-  const int caps[] = {4096, 2048, 8192};
+  const int caps[] = {4096, 2048, 8192, 1024};
   const int chunks[] = {2, 4, 1, 8};
   for (int dim = 0; dim < 4 && s == QSD_OK; ++dim) {
     const int* vals = dim == 0 ? tiles : dim == 1 ? bits : dim == 2 ? caps : chunks;
-    const int nv = dim == 0 || dim == 3 ? 4 : 3;
+    const int nv = dim == 1 ? 3 : 4;
     for (int k = 0; k < nv && s == QSD_OK; ++k) {
       qsd_batch_options o = best;
       int& field = dim == 0 ? o.tile

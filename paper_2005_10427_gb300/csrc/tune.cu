@@ -40,7 +40,7 @@ const int kFirstDigit[] = {0, 6, 5, 7};
 const int kStructure[] = {0, 1};
 const int kDigits[] = {8, 7, 6, 5};
 const int kTiles[] = {0, 4096, 3584, 2048};
-const int kCaps[] = {4096, 2048, 8192};
+const int kCaps[] = {4096, 2048, 8192, 1024};
 const int kChunks[] = {2, 4, 1};
 
 template <typename F>
