@@ -387,10 +387,17 @@ k_chunk_scan(LargeSegs ls, uint32_t* __restrict__ chunk_hist,
 //   writers            write tile k's rows through the inverse permutation.
 // (16 ranking and 15 writing warps for tiles of 2048 entries and more, 8 and
 // 8 for tiles of 1024.)
-// Ranking and writing overlap, and the copies run NS-1 tiles ahead, so
-// neither the ranking latency nor the load latency is on the critical path.
-// Hand-offs use mbarriers (every wait bounded); the rankers synchronise
-// among themselves on named barrier 1.
+// Ranking and writing overlap, and the copies run NS-1 tiles ahead.
+// A slot is released in two parts: the writers write a tile's key rows (the
+// rows its digit is read from) first and then free them, so the next tile
+// of that slot has its key rows loaded and ranked while the other rows of
+// this tile are still being written; its other rows follow once the whole
+// slot is free. (With one slot released as a whole, every slot waited for
+// the load, the ranking and the writing of its tile in turn, and the two
+// slots that fit 24-byte entries could not hide that chain.) In a batch the
+// tiles' key rows differ from tensor to tensor, so there a slot is freed
+// only as a whole. Hand-offs use mbarriers (every wait bounded); the rankers
+// synchronise among themselves on named barrier 1.
 
 // Role sizes: RW ranking warps, WW writing warps, one producer warp.
 template <int RW, int WW>
@@ -409,10 +416,13 @@ struct RowPlan {
   int tail_from;
 };
 
-// One unit of work: tile `k` of chunk `chunk` (chunk >= nchunks: the end).
-struct TileSlot {
-  alignas(16) uint32_t off0[kRadix];  // first tile of a chunk: the chunk's first slot per digit
+// One unit of work: tile `k` of chunk `chunk` (chunk < 0: the end). Tile q
+// is described in entry q % (2 NS) of a ring of these, so the producer can
+// describe a tile once its slot's key rows are free, while the writers still
+// read the description of the tile before it in that slot.
+struct TileMeta {
   int chunk, k, ntile, start, end, lo, hi;
+  unsigned kmask;  // the rows the pass's digit is read from
   RowPlan row[kMaxRows];
   PassTensor it;  // the chunk's tensor: buffers and digit
 };
@@ -421,10 +431,14 @@ template <int T, int NS, int RW>
 struct WsShared {
   uint64_t kfull[NS];    // producer -> rankers: the tile's key rows staged
   uint64_t full[NS];     // producer -> writers: the tile's other rows staged
-  uint64_t empty[NS];    // writers -> producer: staging buffer free
+  uint64_t kempty[NS];   // writers -> producer: the slot's key rows free
+  uint64_t empty[NS];    // writers -> producer: the whole slot free
   uint64_t ranked[2];    // rankers -> writers: destinations ready
   uint64_t consumed[2];  // writers -> rankers: destinations used
-  TileSlot slot[NS];
+  // a chunk's first tile: the chunk's first output slot per digit (loaded
+  // with the key rows; only the rankers read it)
+  alignas(16) uint32_t off0[NS][kRadix];
+  TileMeta meta[2 * NS];
   uint32_t off[kRadix];  // rankers: running output slot per digit of the chunk
   uint32_t warp_hist[RW * kRadix];
   uint32_t rank_tmp[RW];  // block_rank's scan scratch
@@ -477,6 +491,7 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
     for (int s = 0; s < NS; ++s) {
       mbar_init(&S.kfull[s], 32);
       mbar_init(&S.full[s], 32);
+      mbar_init(&S.kempty[s], kWsWriteThreads);
       mbar_init(&S.empty[s], kWsWriteThreads);
     }
     for (int j = 0; j < 2; ++j) {
@@ -489,7 +504,15 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
 
   if (warp == kWsRankWarps + kWsWriteWarps) {
     // ---------------- producer ----------------
-    int ch = 0, k = 0, ntile = 0, issued = 0, drain_from = 0;
+    // One tensor: a tile's key rows load once its slot's key rows are free.
+    // A batch: only once the whole slot is.
+    const bool split = pb.t == nullptr;
+    int ch = 0, k = 0, ntile = 0;
+    // Tiles [0, issued_k) had their key rows' copies started, [0, issued_p)
+    // the other rows'. Before the block exits it waits for the latest phase
+    // of every slot's barriers that copies were started for; skip = the
+    // tile whose phases an end marker in its slot has superseded.
+    int issued_k = 0, issued_p = 0, skip = -1;
     // test-only stall (qsd_debug_set_stall): block 0 arms its first slot
     // for the copies of its first tile but issues none of them
     const bool stall = blockIdx.x == 0 && *(volatile int*)&g_debug_stall == 1;
@@ -500,29 +523,32 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
       idx = __shfl_sync(0xffffffffu, idx, 0);
       return idx < nchunks ? (pb.t ? pb.chunks[idx] : idx) : -1;
     };
+    // lane 0 waits (bounded) and the warp follows its outcome; then every
+    // lane's own wait on the completed phase orders its stores after the
+    // consumers' reads of the slot
+    auto wait_warp = [&](uint64_t* bar, unsigned parity) {
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(bar, parity, status) ? 1 : 0;
+      if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
+      mbar_wait(bar, parity, status);
+      return true;
+    };
     ch = claim_chunk();
     for (int q = 0;; ++q) {
       const int s = q % NS;
+      const unsigned prev = ((q / NS) - 1) & 1;  // phase parity of tile q - NS in slot s
       if (q >= NS) {
-        // lane 0 waits (bounded) and the warp follows its outcome; then every
-        // lane's own wait on the completed phase orders its stores after the
-        // writers' reads of the slot
-        int ok = 1;
-        if (lane == 0) ok = mbar_wait(&S.empty[s], ((q / NS) - 1) & 1, status) ? 1 : 0;
-        if (!__shfl_sync(0xffffffffu, ok, 0)) {
-          drain_from = q - NS;  // tile q - NS (slot s) may still be in flight
-          break;
-        }
-        mbar_wait(&S.empty[s], ((q / NS) - 1) & 1, status);
+        if (!wait_warp(&S.kempty[s], prev)) break;
+        if ((!split || ch < 0) && !wait_warp(&S.empty[s], prev)) break;
       }
-      TileSlot& ts = S.slot[s];
+      TileMeta& ts = S.meta[q % (2 * NS)];
       uint8_t* buf = stage + (size_t)s * bufsz;
       if (ch < 0) {
         if (lane == 0) ts.chunk = -1;
         __syncwarp();
         mbar_arrive(&S.kfull[s]);
         mbar_arrive(&S.full[s]);
-        drain_from = q - NS + 1;  // slot s now holds the end marker
+        skip = q - NS;  // slot s now holds the end marker
         break;
       }
       const ChunkInfo ci = chunk_info(ls, ch);
@@ -550,6 +576,10 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
         }
         ts.row[lane] = rp;
       }
+      // The rows the digit is read from (key rows) are staged first, under
+      // their own barrier, so ranking starts while the other rows still load.
+      unsigned kmask = 0;
+      for (int f = 0; f < ts.it.pd.nfields; ++f) kmask |= 1u << ts.it.pd.f[f].mode;
       if (lane == 0) {
         ts.chunk = ch;
         ts.k = k;
@@ -558,15 +588,11 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
         ts.end = end;
         ts.lo = ci.lo;
         ts.hi = ci.hi;
+        ts.kmask = kmask;
       }
       __syncwarp();
-      // The rows the digit is read from (key rows) are staged first, under
-      // their own barrier, so ranking starts while the other rows still load.
-      unsigned kmask = 0;
-      for (int f = 0; f < ts.it.pd.nfields; ++f) kmask |= 1u << ts.it.pd.f[f].mode;
       const bool is_key = lane < nrows && (kmask >> lane & 1u);
-#pragma unroll
-      for (int phase = 0; phase < 2; ++phase) {
+      auto issue = [&](int phase) {
         uint64_t* bar = phase == 0 ? &S.kfull[s] : &S.full[s];
         // unaligned edges of this phase's rows with plain loads (the whole warp)
         for (int r = 0; r < nrows; ++r) {
@@ -599,17 +625,22 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
         __syncwarp();
         if (lane == 0) mbar_arrive_expect_tx(bar, total);
         else mbar_arrive(bar);
-        const bool skip = stall && q == 0;
-        if (offs && lane == 31 && !skip)
-          bulk_g2s(ts.off0, chunk_off + (size_t)ch * kRadix, kRadix * sizeof(uint32_t), bar);
-        if (mine && bytes && !skip) {
+        const bool no_copy = stall && q == 0;
+        if (offs && lane == 31 && !no_copy)
+          bulk_g2s(S.off0[s], chunk_off + (size_t)ch * kRadix, kRadix * sizeof(uint32_t), bar);
+        if (mine && bytes && !no_copy) {
           const int e = lane < c.order ? 4 : VB;
           bulk_g2s(buf + (size_t)lane * row_slot<T>(4) + rp.off + (size_t)rp.head * e,
                    reinterpret_cast<const void*>(row_base(c, lane) + (uintptr_t)(start + rp.head) * e),
                    bytes, bar);
         }
-      }
-      ++issued;
+      };
+      issue(0);
+      ++issued_k;
+      // the other rows: once the writers are done with the whole slot
+      if (split && q >= NS && !wait_warp(&S.empty[s], prev)) break;
+      issue(1);
+      ++issued_p;
       // next work item
       if (++k >= ntile) {
         k = 0;
@@ -619,11 +650,12 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
     // The block exits only after the bulk copies it started have landed: on
     // a normal end these waits return at once; after a timeout elsewhere they
     // are bounded like every other wait.
-    if (lane == 0)
-      for (int x = drain_from > 0 ? drain_from : 0; x < issued; ++x) {
-        mbar_wait(&S.kfull[x % NS], (x / NS) & 1, status);
-        mbar_wait(&S.full[x % NS], (x / NS) & 1, status);
-      }
+    if (lane == 0) {
+      for (int x = max(0, issued_k - NS); x < issued_k; ++x)
+        if (x != skip) mbar_wait(&S.kfull[x % NS], (x / NS) & 1, status);
+      for (int x = max(0, issued_p - NS); x < issued_p; ++x)
+        if (x != skip) mbar_wait(&S.full[x % NS], (x / NS) & 1, status);
+    }
   } else if (warp < kWsRankWarps) {
     // ---------------- rankers ----------------
     const int w = warp;
@@ -632,7 +664,7 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
       const bool okf = mbar_wait(&S.kfull[s], (q / NS) & 1, status);
       const bool okc = q < 2 || mbar_wait(&S.consumed[j], ((q / 2) - 1) & 1, status);
       if (!(okf && okc)) S.rk_abort = 1;  // the writers stop without writing
-      const TileSlot& ts = S.slot[s];
+      const TileMeta& ts = S.meta[q % (2 * NS)];
       // go: a tile to rank. The rankers share named barrier 1, so they agree
       // on it (at the ranking's first barrier) before any of them leaves.
       const bool go = okf && okc && ts.chunk >= 0;
@@ -663,7 +695,7 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
       const PassDesc& pd = ts.it.pd;
       const int nbins = 1 << pd.bits;
       if (ts.k == 0)  // a new chunk: its first output slot per digit (staged with the tile)
-        for (int d = threadIdx.x; d < nbins; d += kWsRankThreads) S.off[d] = ts.off0[d];
+        for (int d = threadIdx.x; d < nbins; d += kWsRankThreads) S.off[d] = S.off0[s][d];
       for (int d = threadIdx.x; d < nbins; d += kWsRankThreads) {
         uint32_t cnt = S.bin_count[d];
         if (d == kRadix - 1) cnt -= (uint32_t)(T - n_valid);
@@ -682,16 +714,16 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
     for (int q = 0;; ++q) {
       const int s = q % NS, j = q & 1;
       if (!mbar_wait(&S.ranked[j], (q / 2) & 1, status)) break;
-      const TileSlot& ts = S.slot[s];
+      const TileMeta& ts = S.meta[q % (2 * NS)];
       if (ts.chunk < 0 || S.rk_abort) break;
-      // every row of the tile has landed (the key rows, which the rankers
-      // waited for, and the others)
-      if (!mbar_wait(&S.kfull[s], (q / NS) & 1, status) ||
-          !mbar_wait(&S.full[s], (q / NS) & 1, status))
-        break;
+      // the key rows have landed (the rankers waited for them); the level
+      // bytes compare every row, so then all of them must have landed first
+      if (!mbar_wait(&S.kfull[s], (q / NS) & 1, status)) break;
+      if (lv.lev && !mbar_wait(&S.full[s], (q / NS) & 1, status)) break;
       const uint8_t* buf = stage + (size_t)s * bufsz;
       const Cols& c = ts.it.c;
       const int n_valid = ts.end - ts.start, lo = ts.lo, hi = ts.hi;
+      const unsigned kmask = ts.kmask;
       int dst_pos[WITEMS], src_idx[WITEMS];
 #pragma unroll
       for (int k = 0; k < WITEMS; ++k) {
@@ -734,14 +766,22 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
           lv.lev[dst_pos[k]] = (uint8_t)L;
         }
       }
-      for (int r = 0; r < c.order; ++r) {
+      auto write_row = [&](int r) {
         const uint32_t* src =
             reinterpret_cast<const uint32_t*>(buf + (size_t)r * row_slot<T>(4) + ts.row[r].off);
         int32_t* dst = c.out + (int64_t)r * c.out_stride;
 #pragma unroll
         for (int k = 0; k < WITEMS; ++k)
           if (dst_pos[k] >= 0) dst[dst_pos[k]] = (int32_t)src[src_idx[k]];
-      }
+      };
+      // key rows first: once they are written the producer may load the
+      // key rows of the slot's next tile over them
+      for (int r = 0; r < c.order; ++r)
+        if (kmask >> r & 1u) write_row(r);
+      mbar_arrive(&S.kempty[s]);
+      if (!mbar_wait(&S.full[s], (q / NS) & 1, status)) break;
+      for (int r = 0; r < c.order; ++r)
+        if (!(kmask >> r & 1u)) write_row(r);
       if constexpr (VB != 0) {
         using V = typename std::conditional<VB == 8, unsigned long long, uint32_t>::type;
         const V* src = reinterpret_cast<const V*>(buf + (size_t)c.order * row_slot<T>(4) +
