@@ -678,11 +678,10 @@ k_digit_move(const __grid_constant__ PassTensor one, int lay_order, LargeSegs ls
         const DigitField fd = ts.it.pd.f[f];
         const uint32_t* row = reinterpret_cast<const uint32_t*>(
             buf + (size_t)fd.mode * row_slot<T>(4) + ts.row[fd.mode].off);
+        // every position of the row's slot is inside it (positions past the
+        // tile's end read stale words and are overwritten below)
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-          const int pos = w * ITEMS * 32 + i * 32 + lane;
-          if (pos < n_valid) dig[i] |= field_bits(row[pos], fd);
-        }
+        for (int i = 0; i < ITEMS; ++i) dig[i] |= field_bits(row[w * ITEMS * 32 + i * 32 + lane], fd);
       }
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i)
