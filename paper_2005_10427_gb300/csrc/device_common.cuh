@@ -114,11 +114,12 @@ __device__ __forceinline__ uint32_t field_bits(uint32_t c, const DigitField& f) 
 // consecutive ranges and each warp's rounds consecutive 32-element pieces.
 // On return rank[i] is the element's position when the tile is stably sorted
 // by digit; s_bin_start[d] / s_bin_count[d] give each digit's run.
-// Inside a round, the lanes holding equal digits are found from eight
-// ballots, one per digit bit (a lane's peers are the lanes that agree with it
-// on every bit): a fixed cost, where a warp match instruction's cost grows
-// with the number of distinct digits in the warp (measured on this GPU).
-// A per-warp running count per digit in shared memory orders the rounds.
+// Inside a round, the lanes holding equal digits (a lane's peers) come from
+// one ballot for lane 0's digit and a per-warp table of lane masks for the
+// rest (a warp match instruction's cost grows with the number of distinct
+// digits in the warp, eight ballots per round cost twice the table; both
+// measured on this GPU). A per-warp running count per digit in shared memory
+// orders the rounds.
 // Barrier over the first NTHREADS threads: the whole block when BAR == 0,
 // else named barrier BAR.
 template <int BAR, int NTHREADS>
@@ -143,23 +144,6 @@ __device__ __forceinline__ bool group_all(bool pred) {
       : "r"((unsigned)pred), "n"(BAR), "n"(NTHREADS)
       : "memory");
   return r != 0;
-}
-
-// Lanes of the warp whose 8-bit digit equals this lane's: the AND over the
-// digit's bits of the ballot of that bit (or of its complement). The ballots
-// are independent of one another and are all issued first; each is then
-// kept as is where this lane's bit is set and complemented where it is not
-// (XOR with bit - 1, all ones for a clear bit). Measured on this GPU (16
-// warps ranking 3584-entry tiles): 20% fewer cycles than selecting each
-// ballot as it arrives.
-__device__ __forceinline__ uint32_t warp_peers(uint32_t d) {
-  uint32_t bal[kRadixBits];
-#pragma unroll
-  for (int b = 0; b < kRadixBits; ++b) bal[b] = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-  uint32_t m = 0xffffffffu;
-#pragma unroll
-  for (int b = 0; b < kRadixBits; ++b) m &= bal[b] ^ (((d >> b) & 1u) - 1u);
-  return m;
 }
 
 // With BAR != 0 the ranking threads are the first NWARPS warps of the block
@@ -192,9 +176,25 @@ __device__ __forceinline__ bool block_rank(const uint32_t (&dig)[ITEMS],
   for (int k = lane; k < kRadix; k += 32) h[k] = 0;
   __syncwarp();
   const uint32_t lt = (1u << lane) - 1u;
+  // Peers of each round: the lanes that share lane 0's digit from one
+  // ballot; every other lane ORs its bit into the warp's (zeroed) table slot
+  // for its digit, reads the slot back and clears it again, so the table is
+  // zero afterwards for the counts. Measured on this GPU against eight
+  // ballots per round: fewer cycles on every digit distribution tried
+  // (uniform to one value per round), since a round rarely holds many
+  // distinct digits other than its most common one in large groups.
   uint32_t peers[ITEMS];
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) peers[i] = warp_peers(dig[i]);
+  for (int i = 0; i < ITEMS; ++i) {
+    const bool e = dig[i] == __shfl_sync(0xffffffffu, dig[i], 0);
+    const uint32_t z = __ballot_sync(0xffffffffu, e);
+    if (!e) atomicOr(&h[dig[i]], 1u << lane);
+    __syncwarp();
+    peers[i] = e ? z : h[dig[i]];
+    __syncwarp();
+    if (!e) h[dig[i]] = 0;
+    __syncwarp();
+  }
   // one leader per digit and round adds the round's count to the warp's
   // counter; shared atomics of one warp to one address apply in issue order,
   // so each round sees the counts of the rounds before it
