@@ -131,7 +131,7 @@ __device__ __forceinline__ void count4(uint32_t* h, const uint32_t (&e)[4], bool
 // flight per thread), each vector of four consecutive entries counted into
 // the warp's histogram (count4). The vector loops run with warp-uniform
 // bounds so that every lane takes part in count4's warp operations.
-__global__ void __launch_bounds__(kHistThreads)
+__global__ void __launch_bounds__(kHistThreads, 6)
 k_chunk_hist(const __grid_constant__ PassTensor one, LargeSegs ls,
              uint32_t* __restrict__ chunk_hist, uint32_t* __restrict__ group_sum,
              int* __restrict__ claim, PassBatch pb) {
@@ -198,15 +198,15 @@ k_chunk_hist(const __grid_constant__ PassTensor one, LargeSegs ls,
       const uint4* col =
           reinterpret_cast<const uint4*>(c.in + (int64_t)fd.mode * c.in_stride + vbeg);
       // the warp's first lane decides the trip count (lanes differ by < 32)
-      for (int q0 = threadIdx.x; q0 - lane < nvec; q0 += kHistThreads * 8) {
-        uint4 v[8];
+      for (int q0 = threadIdx.x; q0 - lane < nvec; q0 += kHistThreads * 4) {
+        uint4 v[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 4; ++u) {
           const int q = q0 + u * kHistThreads;
           v[u] = q < nvec ? __ldg(col + q) : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 4; ++u) {
           const uint32_t e[4] = {field_bits(v[u].x, fd), field_bits(v[u].y, fd),
                                  field_bits(v[u].z, fd), field_bits(v[u].w, fd)};
           count4(s_hist[w], e, q0 + u * kHistThreads < nvec, lane);
