@@ -313,13 +313,49 @@ k_group_prefix(LargeSegs ls, uint32_t* __restrict__ group_sum) {
 }
 
 // ---------------------------------------------------------------------------
-// Chunk offsets. One block (kRadix threads, one per digit) per chunk group.
-// Over one whole tensor of more than 16 groups the group's first slots come
-// from k_group_prefix; otherwise each block adds up its bucket's groups.
+// Chunk offsets over one whole tensor, after k_group_prefix: one block per
+// chunk group, four parts of 16 chunks each (kRadix threads per part, one per
+// digit). Each part holds its 16 counts in registers (all loads in flight),
+// the parts' sums give each part's first slot, then every chunk's first slot
+// per digit replaces its counts.
+constexpr int kScanParts = 4;
+__global__ void __launch_bounds__(kRadix * kScanParts)
+k_chunk_scan_parts(LargeSegs ls, uint32_t* __restrict__ chunk_hist,
+                   const uint32_t* __restrict__ group_sum) {
+  constexpr int kPer = kGroupChunks / kScanParts;
+  static_assert(kPer * kScanParts == kGroupChunks, "parts cover a group");
+  __shared__ uint32_t s_part[kScanParts][kRadix];
+  const int d = threadIdx.x % kRadix, part = threadIdx.x / kRadix;
+  const int ng = n_groups(ls), nc = n_chunks(ls);
+  for (int G = blockIdx.x; G < ng; G += gridDim.x) {
+    const int c0 = G * kGroupChunks + part * kPer;
+    uint32_t h[kPer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      h[k] = c0 + k < nc ? chunk_hist[(size_t)(c0 + k) * kRadix + d] : 0u;
+      sum += h[k];
+    }
+    s_part[part][d] = sum;
+    __syncthreads();
+    uint32_t off = group_sum[(size_t)G * kRadix + d];  // k_group_prefix's first slot
+    for (int q = 0; q < part; ++q) off += s_part[q][d];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k)
+      if (c0 + k < nc) {
+        chunk_hist[(size_t)(c0 + k) * kRadix + d] = off;
+        off += h[k];
+      }
+    __syncthreads();  // s_part is reused by the next group
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Chunk offsets. One block (kRadix threads, one per digit) per chunk group,
+// each block adding up its bucket's groups (buckets, batches, and tensors of
+// at most 16 groups; larger whole tensors take k_chunk_scan_parts).
 __global__ void __launch_bounds__(kRadix)
 k_chunk_scan(LargeSegs ls, uint32_t* __restrict__ chunk_hist,
-             const uint32_t* __restrict__ group_sum, PassBatch pb, int prefixed) {
-  // prefixed: group_sum holds k_group_prefix's first slots (one whole tensor)
+             const uint32_t* __restrict__ group_sum, PassBatch pb) {
   __shared__ uint32_t s_tmp[kRadix / 32 + 1];
   const int d = threadIdx.x;
   const int ng_all = pb.t ? pb.counters[kCntPassGroups + pb.pass] : n_groups(ls);
@@ -344,21 +380,16 @@ k_chunk_scan(LargeSegs ls, uint32_t* __restrict__ chunk_hist,
       lo = se.x;
     }
     (void)s;
-    uint32_t off;
-    if (prefixed) {
-      off = group_sum[(size_t)G * kRadix + d];  // k_group_prefix's first slot
-    } else {
-      // bucket total and the sum over the bucket's earlier groups, per digit
-      uint32_t total = 0, prior = 0;
-      for (int g = gb; g < gb + ng; ++g) {
-        const uint32_t v = group_sum[(size_t)g * kRadix + d];
-        total += v;
-        if (g < G) prior += v;
-      }
-      uint32_t tot_all;
-      const uint32_t below = block_exclusive_sum<kRadix / 32>(total, s_tmp, &tot_all);
-      off = (uint32_t)lo + below + prior;
+    // bucket total and the sum over the bucket's earlier groups, per digit
+    uint32_t total = 0, prior = 0;
+    for (int g = gb; g < gb + ng; ++g) {
+      const uint32_t v = group_sum[(size_t)g * kRadix + d];
+      total += v;
+      if (g < G) prior += v;
     }
+    uint32_t tot_all;
+    const uint32_t below = block_exclusive_sum<kRadix / 32>(total, s_tmp, &tot_all);
+    uint32_t off = (uint32_t)lo + below + prior;
     const int c0 = cb + (G - gb) * kGroupChunks;
     const int c1 = min(c0 + kGroupChunks, cb + nc);
     for (int c = c0; c < c1; c += 8) {
@@ -908,8 +939,14 @@ cudaError_t launch_chunk_scan(const LargeSegs& ls, uint32_t* chunk_hist,
   if (grid < 1) grid = 1;
   // with few groups each block's own sum over them is cheaper than a launch more
   const int prefixed = ls.single && !pb.t && max_groups > 16;
-  if (prefixed) k_group_prefix<<<1, kRadix * kPrefixParts, 0, stream>>>(ls, group_sum);
-  k_chunk_scan<<<grid, kRadix, 0, stream>>>(ls, chunk_hist, group_sum, pb, prefixed);
+  if (prefixed) {
+    k_group_prefix<<<1, kRadix * kPrefixParts, 0, stream>>>(ls, group_sum);
+    int g4 = 2 * sm_count();
+    if (g4 > max_groups) g4 = max_groups;
+    k_chunk_scan_parts<<<g4, kRadix * kScanParts, 0, stream>>>(ls, chunk_hist, group_sum);
+    return cudaGetLastError();
+  }
+  k_chunk_scan<<<grid, kRadix, 0, stream>>>(ls, chunk_hist, group_sum, pb);
   return cudaGetLastError();
 }
 
