@@ -160,6 +160,19 @@ def test_tile_sizes_and_chunk_lengths(qsd, tile, chunk_tiles):
         check(qsd, coords, vals, dims, sigma, tile=tile, chunk_tiles=chunk_tiles)
 
 
+@pytest.mark.parametrize("extra", [0, 1, 21, 40])
+def test_many_chunk_groups_with_ragged_parts(qsd, extra):
+    # a whole tensor of more than 16 chunk groups takes the group prefix and
+    # the four-part offset scan: 17 full groups of 64 one-tile chunks, then
+    # `extra` chunks and a ragged last one (last group ending inside part 0,
+    # 1 or 2 of its four 16-chunk parts)
+    dims = [5000, 60000, 9]
+    nnz = (17 * 64 + extra) * 1024 + 77
+    coords, vals = tensor(dims, nnz, seed=extra + 5, zipf=1.1)
+    for sigma in [(1, 0, 2), (2, 1, 0)]:
+        check(qsd, coords, vals, dims, sigma, tile=1024, chunk_tiles=1)
+
+
 @pytest.mark.parametrize("r", [3, 4])
 def test_global_groups_give_the_same_result(qsd, r):
     # groups with a prefix run as global sorts by (prefix, key)
