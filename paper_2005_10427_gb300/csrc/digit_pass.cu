@@ -13,7 +13,9 @@
 //                  the sum of its chunks' histograms;
 //   k_chunk_scan   per chunk group: every chunk's first output slot for each
 //                  digit = bucket start + entries of smaller digits in the
-//                  bucket + entries of the same digit in earlier chunks;
+//                  bucket + entries of the same digit in earlier chunks (over
+//                  a whole tensor of many groups: k_group_prefix, then
+//                  k_chunk_scan_parts);
 //   k_digit_move   per chunk (claimed dynamically): tiles of the chunk are
 //                  staged in shared memory by bulk asynchronous copies (the
 //                  next tile's copies overlap the current tile), ranked
