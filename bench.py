@@ -234,9 +234,13 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gnnz/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic",
-            "config": {"workload": wl["name"], "nnz": nnz, "sample_nnz": sample,
-                       "perms": [list(p) for p in perms]},
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32+f64" if vals.dtype.itemsize == 8 else "int32+f32",
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "dims": list(wl["dims"]), "nnz": nnz,
+                       "sample_nnz": sample, "dists": [list(x) for x in wl["dists"]],
+                       "perms": [list(p) for p in perms],
+                       "input_order": list(range(len(wl["dims"])))},
             "cpu_baseline": {"value": value, "unit": "Gnnz/s", "cores": 1, "kind": "oracle",
                              "sample": f"{sample} entries sorted in input order (the workload's "
                                        f"generator at this count), {len(perms)} target orders "
